@@ -1,0 +1,204 @@
+/*
+ * pdst.h -- C ABI of the B300 library for the regularised traveltime
+ * least-squares solve of direct surface-wave tomography (pDSurfTomo,
+ * arXiv 2604.11920).
+ *
+ * The library builds the sensitivity matrix G of Eq. 5-6 on the GPU from ray
+ * geometry and a period depth-kernel table, and solves
+ *
+ *     min_m ||G m - d||^2 + w^2 ||L m||^2 + lambda^2 ||m||^2          (*)
+ *
+ * (the least-squares problem of Eq. 6, "Solver for the Large-scale Linear
+ * System", with a smoothing term w L, L the 3-D 7-point Laplacian, and
+ * damping lambda) by LSQR (Paige & Saunders 1982, the solver the paper cites
+ * beside LSMR), entirely in hand-written sm_103a kernels.
+ *
+ * Conventions
+ *  - Grid nx x ny x nz, cell size dx_km, layer thickness dz_km.  Model column
+ *    j = (iy*nx + ix)*nz + k (depth fastest, Eq. 7).  Data rows follow the
+ *    order of the paths passed to pdst_build_G.
+ *  - Pointers named *_host are host memory; *_dev are device memory on the
+ *    handle's device.  All device buffers passed in stay owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that return results to the host synchronise that stream.
+ *  - Every function returns a pdst_status; on error, pdst_last_error_string()
+ *    returns a message for the calling thread.  Arguments are checked on the
+ *    host before any launch; no function aborts the process.
+ *  - A handle may be used by one host thread at a time; solves on the same
+ *    handle must not overlap (they share the handle's workspace).
+ */
+#ifndef PDST_H
+#define PDST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdst_handle *pdst_handle_t;
+
+typedef enum {
+    PDST_OK = 0,
+    PDST_ERR_ARG = 1,           /* invalid argument (checked on the host) */
+    PDST_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    PDST_ERR_OOM = 3,           /* device allocation failed */
+    PDST_ERR_BREAKDOWN = 4,     /* NaN/Inf met in the LSQR recurrence */
+    PDST_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    PDST_ERR_NOT_CONVERGED = 6, /* reserved: a solve reports istop = 7 instead */
+    PDST_ERR_LIMIT = 7,         /* a documented size limit was exceeded */
+    PDST_ERR_STATE = 8          /* the requested form was not built into the handle */
+} pdst_status;
+
+/* Precision of stored G values and of the LSQR vectors u, v. */
+typedef enum {
+    PDST_F64 = 0,   /* FP64 values, FP64 vectors (the plain form) */
+    PDST_F32 = 1,   /* FP32 values, FP32 vectors, FP32 accumulation */
+    PDST_BF16 = 2   /* BF16 values, FP32 vectors, FP32 accumulation */
+} pdst_dtype;
+
+/* Index layout used by the sparse products. */
+typedef enum {
+    PDST_FMT_ELEMENT = 0, /* CSR + CSC, one int32 index per stored entry */
+    PDST_FMT_BLOCKED = 1  /* one int32 index per (row, cell) run of nz entries */
+} pdst_format;
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx_km;     /* horizontal cell size (km) */
+    double dz_km;     /* layer thickness (km); not used by the assembly itself */
+} pdst_grid;
+
+typedef struct {
+    uint32_t value_dtypes; /* bit mask of (1u << pdst_dtype) value copies to keep; 0 = F64|F32 */
+    uint32_t formats;      /* bit mask of (1u << pdst_format) index layouts; 0 = both */
+} pdst_build_opts;
+
+/*
+ * Build G on the device (Eq. 5-7, synthetic form).
+ *
+ * Row r of G is the ray of path r at period path_period[r]:
+ *   G[r, h*nz + k] = l_h(r) * kdz[path_period[r]*nz + k]
+ * for every horizontal cell h = iy*nx + ix the ray crosses, where l_h(r) is
+ * the ray length inside h.  The ray is the quadratic Bezier curve with
+ * control points ctrl_host[6r .. 6r+5] = (P0x, P0y, P1x, P1y, P2x, P2y) in km;
+ * it is cut into N = max(1, ceil(4 * (|P1-P0| + |P2-P1|) / dx)) chords of
+ * equal parameter step, each chord's length goes to the cell holding its
+ * midpoint (clamped into the grid), and lengths are summed per cell in chord
+ * order.  A ray of zero length gives an empty row.  Every hit cell stores all
+ * nz depth entries (explicit zeros included), cells ascending within a row.
+ * The FP64 values equal, bit for bit, the same recipe evaluated with one
+ * rounding per written operation (no fused multiply-add).
+ *
+ * Inputs are host arrays, copied to the device; n_paths may be 0.  The call
+ * is synchronous.  Errors: PDST_ERR_ARG (bad sizes, non-finite coordinates,
+ * period index out of range), PDST_ERR_LIMIT (a ray that may cross more
+ * distinct cells than the per-warp list holds, about 17,000), PDST_ERR_OOM,
+ * PDST_ERR_CUDA.  On success *out owns all device memory of G; release it
+ * with pdst_destroy.
+ */
+pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths, const double *ctrl_host,
+                         const int32_t *path_period_host, int32_t n_periods,
+                         const double *kdz_host, const pdst_build_opts *opts,
+                         void *stream, pdst_handle_t *out);
+
+/* Release a handle and all device memory it owns.  NULL is accepted. */
+pdst_status pdst_destroy(pdst_handle_t h);
+
+/* Sizes: rows m, columns n, stored entries nnz (any pointer may be NULL). */
+pdst_status pdst_G_info(pdst_handle_t h, int64_t *m, int32_t *n, int64_t *nnz);
+
+/*
+ * Copy G (CSR) or G^T (CSR of the transpose, i.e. CSC of G; rows ascending
+ * within each column) to caller-allocated host arrays: ptr (m+1 or n+1),
+ * idx (nnz), val (nnz, the stored values of `dtype` widened to FP64).  Any
+ * output pointer may be NULL.  PDST_ERR_STATE if that dtype was not kept.
+ * The index arrays are built from the blocked layout when the element layout
+ * was not kept.  Synchronous.
+ */
+pdst_status pdst_G_export_csr(pdst_handle_t h, int32_t dtype, int64_t *row_ptr_host,
+                              int32_t *col_host, double *val_host);
+pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t *col_ptr_host,
+                              int32_t *row_host, double *val_host);
+
+/*
+ * y = G x (trans = 0; x has n entries, y has m) or y = G^T x (trans = 1),
+ * with the stored values of `dtype`, FP64 input/output vectors (device) and
+ * FP64 accumulation.  Gather-only kernels (CSR for G, CSC for G^T), no
+ * atomics.  Asynchronous on `stream`.
+ */
+pdst_status pdst_apply_G(pdst_handle_t h, int32_t dtype, int32_t trans, const double *x_dev,
+                         double *y_dev, void *stream);
+
+typedef struct {
+    int32_t dtype;     /* pdst_dtype of values and u/v vectors (default PDST_F64) */
+    int32_t format;    /* pdst_format (default PDST_FMT_ELEMENT) */
+    double atol;       /* < 0: use tol */
+    double btol;       /* < 0: use tol */
+    double conlim;     /* <= 0: 1e8 */
+    int32_t precond;   /* 0 none; 1 right diagonal scaling set by pdst_set_col_scaling */
+    int32_t kblock;    /* iterations per graph launch (<= 0: 16) */
+    int32_t use_graph; /* 1 (default): CUDA graph replay; 0: plain launches */
+    int32_t reserved;
+    double *rnorm_hist_dev; /* optional device array (itmax): ||r|| after each iteration */
+} pdst_lsqr_opts;
+
+/* Fill *o with the defaults listed above. */
+void pdst_lsqr_opts_default(pdst_lsqr_opts *o);
+
+typedef struct {
+    int32_t iters;   /* iterations performed */
+    int32_t istop;   /* 0 x = 0 is exact; 1 ||r|| <= btol||b|| + atol||A||||x||;
+                        2 ||A^T r|| <= atol ||A|| ||r||; 3 cond(A) >= conlim;
+                        4-6 the same at machine precision; 7 itmax reached */
+    double rnorm;    /* estimate of ||[d; 0; 0] - [G; w L; lambda I] m|| (or scaled form) */
+    double arnorm;   /* estimate of ||A^T r|| */
+    double anorm;    /* estimate of ||A||_F */
+    double acond;    /* estimate of cond(A) */
+    double xnorm;    /* estimate of ||x|| (of y when scaled) */
+    double bnorm;    /* ||d|| */
+} pdst_lsqr_info;
+
+/*
+ * Solve (*) by LSQR (Paige & Saunders 1982) on the augmented operator
+ * A = [G; w L] with damping lambda in the recurrence, or, with
+ * opts->precond = 1 and a scaling D set by pdst_set_col_scaling, on
+ * A_D = [G D; w L D; lambda D] with no recurrence damping and m = D y (the
+ * same minimiser).  d_dev: m_rows FP64 (device, caller-owned).  m_out_dev: n
+ * FP64 (device, caller-owned).  tol sets atol = btol unless opts overrides;
+ * conlim defaults to 1e8.  The Golub-Kahan scalars, the rotations, the norm
+ * estimates and the x/w update are FP64 in every dtype.  info (host) may be
+ * NULL.  The call is synchronous on `stream`.
+ * Errors: PDST_ERR_ARG, PDST_ERR_STATE (dtype/format not built, or precond
+ * requested without a scaling), PDST_ERR_BREAKDOWN, PDST_ERR_CUDA.
+ */
+pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lambda,
+                      int32_t itmax, double tol, double *m_out_dev, pdst_lsqr_info *info,
+                      const pdst_lsqr_opts *opts, void *stream);
+
+/* Same as pdst_lsqr with host d and m (pinned or pageable): copies d in and
+ * m out inside the call (the end-to-end path). */
+pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w, double lambda,
+                           int32_t itmax, double tol, double *m_out_host,
+                           pdst_lsqr_info *info, const pdst_lsqr_opts *opts, void *stream);
+
+/*
+ * Right diagonal scaling m = D y for pdst_lsqr with precond = 1.
+ * D_dev: n FP64 positive entries (device, copied into the handle), or NULL to
+ * use the column-norm scaling D_j = 1 / ||[G; w L; lambda I]_{:,j}|| of the
+ * augmented operator for the given w, lambda.  Synchronous.
+ */
+pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev, double w, double lambda,
+                                 void *stream);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *pdst_last_error_string(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t pdst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDST_H */

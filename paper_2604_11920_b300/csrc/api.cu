@@ -1,0 +1,146 @@
+// api.cu -- handle lifetime, error reporting, inspection and export entry
+// points of the C ABI declared in include/pdst.h.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pdst {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static double bf16_to_double(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
+// Copy `count` stored values of `dtype` starting at `src` to host FP64.
+static pdst_status values_to_host(int dtype, const void *src, int64_t count, double *out) {
+    if (count == 0) return PDST_OK;
+    if (dtype == PDST_F64) {
+        PDST_CUDA(cudaMemcpy(out, src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    } else if (dtype == PDST_F32) {
+        std::vector<float> tmp(count);
+        PDST_CUDA(cudaMemcpy(tmp.data(), src, sizeof(float) * count, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < count; ++i) out[i] = (double)tmp[i];
+    } else {
+        std::vector<uint16_t> tmp(count);
+        PDST_CUDA(cudaMemcpy(tmp.data(), src, sizeof(uint16_t) * count, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < count; ++i) out[i] = bf16_to_double(tmp[i]);
+    }
+    return PDST_OK;
+}
+
+template <class T> static pdst_status d2h(std::vector<T> &v, const DevBuf &b, int64_t count) {
+    v.resize(count);
+    if (count) PDST_CUDA(cudaMemcpy(v.data(), b.p, sizeof(T) * count, cudaMemcpyDeviceToHost));
+    return PDST_OK;
+}
+
+}  // namespace pdst
+
+using namespace pdst;
+
+extern "C" const char *pdst_last_error_string(void) { return g_err; }
+
+extern "C" int32_t pdst_version(void) { return 10000; }
+
+extern "C" pdst_status pdst_destroy(pdst_handle_t h) {
+    if (!h) return PDST_OK;
+    int dev = 0;
+    const int hdev = h->device;
+    cudaGetDevice(&dev);
+    if (dev != hdev) cudaSetDevice(hdev);
+    delete h;
+    if (dev != hdev) cudaSetDevice(dev);
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_G_info(pdst_handle_t h, int64_t *m, int32_t *n, int64_t *nnz) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_G_info: handle is NULL");
+    if (m) *m = h->m;
+    if (n) *n = h->n;
+    if (nnz) *nnz = h->nnz;
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_G_export_csr(pdst_handle_t h, int32_t dtype, int64_t *row_ptr_host,
+                                         int32_t *col_host, double *val_host) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_G_export_csr: handle is NULL");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_G_export_csr: unknown dtype");
+    if (val_host && !h->vals[dtype].present) {
+        set_error("pdst_G_export_csr: values of dtype %d were not kept", dtype);
+        return PDST_ERR_STATE;
+    }
+    const int nz = h->nz;
+    if (row_ptr_host || col_host) {
+        std::vector<int64_t> cptr;
+        PDST_TRY(d2h(cptr, h->row_cptr, h->m + 1));
+        if (row_ptr_host)
+            for (int64_t r = 0; r <= h->m; ++r) row_ptr_host[r] = (int64_t)nz * cptr[r];
+        if (col_host) {
+            std::vector<int32_t> cells;
+            PDST_TRY(d2h(cells, h->row_cells, h->U));
+            for (int64_t e = 0; e < h->U; ++e)
+                for (int k = 0; k < nz; ++k) col_host[(int64_t)nz * e + k] = cells[e] * nz + k;
+        }
+    }
+    if (val_host) PDST_TRY(values_to_host(dtype, h->vals[dtype].csr.p, h->nnz, val_host));
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t *col_ptr_host,
+                                         int32_t *row_host, double *val_host) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_G_export_csc: handle is NULL");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_G_export_csc: unknown dtype");
+    if (val_host && !h->vals[dtype].present) {
+        set_error("pdst_G_export_csc: values of dtype %d were not kept", dtype);
+        return PDST_ERR_STATE;
+    }
+    const bool elem = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
+    if (col_ptr_host) {
+        if (elem) {
+            PDST_CUDA(cudaMemcpy(col_ptr_host, h->col_ptr.p, sizeof(int64_t) * ((int64_t)h->n + 1),
+                                 cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<int64_t> rptr;
+            std::vector<int32_t> cnt;
+            PDST_TRY(d2h(rptr, h->cell_rptr, (int64_t)h->H + 1));
+            PDST_TRY(d2h(cnt, h->cell_cnt, h->H));
+            for (int32_t c = 0; c < h->H; ++c)
+                for (int k = 0; k < h->nz; ++k)
+                    col_ptr_host[(int64_t)c * h->nz + k] =
+                        (int64_t)h->nz * rptr[c] + (int64_t)k * cnt[c];
+            col_ptr_host[h->n] = h->nnz;
+        }
+    }
+    if (row_host) {
+        if (elem) {
+            if (h->nnz)
+                PDST_CUDA(cudaMemcpy(row_host, h->row_idx.p, sizeof(int32_t) * h->nnz,
+                                     cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<int64_t> rptr;
+            std::vector<int32_t> cnt, rows;
+            PDST_TRY(d2h(rptr, h->cell_rptr, (int64_t)h->H + 1));
+            PDST_TRY(d2h(cnt, h->cell_cnt, h->H));
+            PDST_TRY(d2h(rows, h->cell_rows, h->U));
+            for (int32_t c = 0; c < h->H; ++c)
+                for (int k = 0; k < h->nz; ++k)
+                    for (int q = 0; q < cnt[c]; ++q)
+                        row_host[(int64_t)h->nz * rptr[c] + (int64_t)k * cnt[c] + q] =
+                            rows[rptr[c] + q];
+        }
+    }
+    if (val_host) PDST_TRY(values_to_host(dtype, h->vals[dtype].csc.p, h->nnz, val_host));
+    return PDST_OK;
+}

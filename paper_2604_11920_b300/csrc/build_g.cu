@@ -1,0 +1,626 @@
+// build_g.cu -- on-device assembly of the sensitivity matrix G (Eq. 5-7,
+// synthetic form) and of its transpose.
+//
+// G[r, h*nz + k] = l_h(r) * Kdz[t(r)][k]: every horizontal cell h that ray r
+// crosses contributes all nz depth columns (Eq. 5), columns ordered depth
+// fastest (Eq. 7).  l_h(r) comes from cutting the quadratic Bezier ray into
+// N = max(1, ceil(4 * polygon_length / dx)) equal-parameter chords, giving
+// each chord to the cell of its midpoint (clamped into the grid) and summing
+// the chord lengths of a cell in chord order.
+//
+// Every floating-point operation of that recipe is written with an explicit
+// round-to-nearest intrinsic (no fused multiply-add), so the FP64 values are
+// reproducible bit for bit by any IEEE implementation of the same recipe.
+//
+// Layout produced (all device memory owned by the handle):
+//   row_cptr[m+1] int64, row_cells[U] int32   cell-level CSR (runs of nz entries)
+//   cell_rptr[H+1] int64, cell_rows[U] int32  cell-level transpose, rows ascending
+//   vals[d].csr[nnz], vals[d].csc[nnz]         values in CSR / CSC order per dtype
+//   row_ptr, col, col_ptr, row_idx             element indices (PDST_FMT_ELEMENT)
+// with nnz = nz * U and the CSC of column j = h*nz + k starting at
+// nz*cell_rptr[h] + k*cnt[h].
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pdst {
+
+namespace {
+
+struct Ray {
+    double x0, y0, x1, y1, x2, y2;
+};
+
+__device__ __forceinline__ void bezier_pt(const Ray &c, double tau, double &x, double &y) {
+    double a = __dsub_rn(1.0, tau);
+    double b0 = __dmul_rn(a, a);
+    double b1 = __dmul_rn(__dmul_rn(2.0, tau), a);
+    double b2 = __dmul_rn(tau, tau);
+    x = __dadd_rn(__dadd_rn(__dmul_rn(b0, c.x0), __dmul_rn(b1, c.x1)), __dmul_rn(b2, c.x2));
+    y = __dadd_rn(__dadd_rn(__dmul_rn(b0, c.y0), __dmul_rn(b1, c.y1)), __dmul_rn(b2, c.y2));
+}
+
+__device__ __forceinline__ double hyp(double ex, double ey) {
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+}
+
+__device__ __forceinline__ int64_t chord_count_dev(const Ray &c, double dx) {
+    double lp = __dadd_rn(hyp(__dsub_rn(c.x1, c.x0), __dsub_rn(c.y1, c.y0)),
+                          hyp(__dsub_rn(c.x2, c.x1), __dsub_rn(c.y2, c.y1)));
+    if (!(lp > 0.0)) return 0;
+    double nf = ceil(__ddiv_rn(__dmul_rn(4.0, lp), dx));
+    if (nf < 1.0) nf = 1.0;
+    return (int64_t)nf;
+}
+
+__device__ __forceinline__ int cell_of(double coord, double dx, int ncell) {
+    double f = floor(__ddiv_rn(coord, dx));
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(ncell - 1)) f = (double)(ncell - 1);
+    return (int)f;
+}
+
+// One warp walks one ray.  The 32 lanes evaluate 32 consecutive chords at a
+// time; the per-cell sums are then advanced in chord order (every lane holds
+// the same running sum, so the result does not depend on the lane).  The
+// distinct cells live in a per-warp shared-memory list of capacity `cap`.
+// Returns the number of distinct cells (> cap means the list overflowed).
+__device__ int walk_ray_warp(const Ray &c, int nx, int ny, double dx, int cap, int *lc,
+                             double *la) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int64_t N = chord_count_dev(c, dx);
+    int u = 0, cur_slot = -1, cur_cell = -1;
+    double cur = 0.0;
+    double cx, cy;
+    bezier_pt(c, 0.0, cx, cy);
+    for (int64_t base = 0; base < N; base += 32) {
+        int64_t s = base + lane + 1;
+        bool valid = s <= N;
+        double qx = 0.0, qy = 0.0;
+        if (valid) bezier_pt(c, __ddiv_rn((double)s, (double)N), qx, qy);
+        double px = __shfl_up_sync(full, qx, 1), py = __shfl_up_sync(full, qy, 1);
+        if (lane == 0) {
+            px = cx;
+            py = cy;
+        }
+        double len = 0.0;
+        int cell = 0;
+        if (valid) {
+            len = hyp(__dsub_rn(qx, px), __dsub_rn(qy, py));
+            double mx = __dmul_rn(0.5, __dadd_rn(px, qx));
+            double my = __dmul_rn(0.5, __dadd_rn(py, qy));
+            cell = cell_of(my, dx, ny) * nx + cell_of(mx, dx, nx);
+        }
+        cx = __shfl_sync(full, qx, 31);
+        cy = __shfl_sync(full, qy, 31);
+        int nvalid = (int)((N - base) < 32 ? (N - base) : 32);
+        for (int j = 0; j < nvalid; ++j) {
+            int cj = __shfl_sync(full, cell, j);
+            double lj = __shfl_sync(full, len, j);
+            if (cj != cur_cell) {
+                if (lane == 0 && cur_slot >= 0 && cur_slot < cap) la[cur_slot] = cur;
+                __syncwarp();
+                int found = -1;
+                int lim = u < cap ? u : cap;
+                for (int q0 = 0; q0 < lim; q0 += 32) {
+                    int q = q0 + lane;
+                    unsigned b = __ballot_sync(full, q < lim && lc[q] == cj);
+                    if (b) {
+                        found = q0 + __ffs(b) - 1;
+                        break;
+                    }
+                }
+                if (found >= 0) {
+                    cur = la[found];
+                    cur_slot = found;
+                } else {
+                    if (lane == 0 && u < cap) lc[u] = cj;
+                    cur_slot = u;
+                    ++u;
+                    cur = 0.0;
+                }
+                cur_cell = cj;
+                __syncwarp();
+            }
+            cur = __dadd_rn(cur, lj);
+        }
+    }
+    if (lane == 0 && cur_slot >= 0 && cur_slot < cap) la[cur_slot] = cur;
+    __syncwarp();
+    return u;
+}
+
+__device__ __forceinline__ Ray load_ray(const double *ctrl, int64_t r) {
+    const double *p = ctrl + 6 * r;
+    return Ray{p[0], p[1], p[2], p[3], p[4], p[5]};
+}
+
+// Pass 1: distinct cells per row.
+__global__ void k_count_cells(int64_t m, const double *__restrict__ ctrl, int nx, int ny,
+                              double dx, int cap, int32_t *__restrict__ cnt, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    double *la = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
+    int *lc = reinterpret_cast<int *>(smem + (size_t)wpb * cap * sizeof(double)) + (size_t)warp * cap;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < m; r += (int64_t)gridDim.x * wpb) {
+        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, cap, lc, la);
+        if ((threadIdx.x & 31) == 0) {
+            cnt[r] = u;
+            if (u > cap) atomicExch(err, 1);
+        }
+    }
+}
+
+// Pass 2: walk again, sort the row's cells ascending (rank of unique keys)
+// and write cells, per-cell lengths and the owning row of every run.
+__global__ void k_fill_cells(int64_t m, const double *__restrict__ ctrl, int nx, int ny,
+                             double dx, int cap, const int64_t *__restrict__ cptr,
+                             int32_t *__restrict__ cells, double *__restrict__ lens,
+                             int32_t *__restrict__ run_row, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *la = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
+    int *lc = reinterpret_cast<int *>(smem + (size_t)wpb * cap * sizeof(double)) + (size_t)warp * cap;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < m; r += (int64_t)gridDim.x * wpb) {
+        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, cap, lc, la);
+        int64_t base = cptr[r];
+        if (u > cap || (int64_t)u != cptr[r + 1] - base) {
+            if (lane == 0) atomicExch(err, 2);
+            continue;
+        }
+        for (int q = lane; q < u; q += 32) {
+            int key = lc[q];
+            int rank = 0;
+            for (int j = 0; j < u; ++j) rank += lc[j] < key;
+            cells[base + rank] = key;
+            lens[base + rank] = la[q];
+            run_row[base + rank] = (int32_t)r;
+        }
+        __syncwarp();
+    }
+}
+
+// vals[nz*e + k] = l_e * Kdz[t(row(e))][k] in FP64, plus narrower copies.
+__global__ void k_expand_values(int64_t U, int nz, const double *__restrict__ lens,
+                                const int32_t *__restrict__ run_row,
+                                const int32_t *__restrict__ row_period,
+                                const double *__restrict__ kdz, double *v64, float *v32,
+                                __nv_bfloat16 *vbf) {
+    int64_t total = U * nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = i / nz;
+        int k = (int)(i - e * nz);
+        int t = row_period[run_row[e]];
+        double v = __dmul_rn(lens[e], kdz[(int64_t)t * nz + k]);
+        if (v64) v64[i] = v;
+        if (v32) v32[i] = __double2float_rn(v);
+        if (vbf) vbf[i] = __double2bfloat16(v);
+    }
+}
+
+__global__ void k_cell_count(int64_t U, const int32_t *__restrict__ cells, int32_t *cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < U;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[cells[e]], 1);
+}
+
+// Histogram of cells per chunk of `ch` consecutive rows.
+__global__ void k_chunk_count(int64_t U, int ch, int H, const int32_t *__restrict__ cells,
+                              const int32_t *__restrict__ run_row, int32_t *chunk_cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < U;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&chunk_cnt[(int64_t)(run_row[e] / ch) * H + cells[e]], 1);
+}
+
+// Turn per-chunk counts into absolute start positions, chunk by chunk.
+__global__ void k_chunk_scan(int64_t nchunk, int H, const int64_t *__restrict__ cell_rptr,
+                             const int32_t *__restrict__ chunk_cnt, int64_t *chunk_base) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    int64_t run = cell_rptr[h];
+    for (int64_t c = 0; c < nchunk; ++c) {
+        int64_t idx = c * H + h;
+        int32_t t = chunk_cnt[idx];
+        chunk_base[idx] = run;
+        run += t;
+    }
+}
+
+// One block per chunk places its rows in order: rows of a chunk are visited
+// one after another, the runs of one row in parallel (distinct cells).
+__global__ void k_chunk_place(int64_t m, int ch, int H, const int64_t *__restrict__ row_cptr,
+                              const int32_t *__restrict__ cells, int64_t *chunk_base,
+                              int32_t *__restrict__ cell_rows, int64_t *__restrict__ run_pos) {
+    int64_t c = blockIdx.x;
+    int64_t r0 = c * ch, r1 = r0 + ch < m ? r0 + ch : m;
+    int64_t *base = chunk_base + c * H;
+    for (int64_t r = r0; r < r1; ++r) {
+        for (int64_t e = row_cptr[r] + threadIdx.x; e < row_cptr[r + 1]; e += blockDim.x) {
+            int h = cells[e];
+            int64_t pos = base[h];
+            base[h] = pos + 1;
+            cell_rows[pos] = (int32_t)r;
+            run_pos[e] = pos;
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void k_csc_values(int64_t U, int nz, const int32_t *__restrict__ cells,
+                             const int64_t *__restrict__ run_pos,
+                             const int64_t *__restrict__ cell_rptr,
+                             const int32_t *__restrict__ cell_cnt, const T *__restrict__ csr,
+                             T *__restrict__ csc) {
+    int64_t total = U * nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = i / nz;
+        int k = (int)(i - e * nz);
+        int h = cells[e];
+        int64_t start = cell_rptr[h];
+        csc[(int64_t)nz * start + (int64_t)k * cell_cnt[h] + (run_pos[e] - start)] = csr[i];
+    }
+}
+
+__global__ void k_elem_csr(int64_t m, int64_t U, int nz, const int64_t *__restrict__ row_cptr,
+                           const int32_t *__restrict__ cells, int64_t *row_ptr, int32_t *col) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = tid; r <= m; r += stride) row_ptr[r] = (int64_t)nz * row_cptr[r];
+    for (int64_t i = tid; i < U * nz; i += stride) {
+        int64_t e = i / nz;
+        col[i] = cells[e] * nz + (int)(i - e * nz);
+    }
+}
+
+__global__ void k_elem_csc(int64_t U, int H, int nz, const int32_t *__restrict__ cells,
+                           const int32_t *__restrict__ run_row,
+                           const int64_t *__restrict__ run_pos,
+                           const int64_t *__restrict__ cell_rptr,
+                           const int32_t *__restrict__ cell_cnt, int64_t *col_ptr,
+                           int32_t *row_idx) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t n = (int64_t)H * nz;
+    for (int64_t j = tid; j <= n; j += stride) {
+        if (j == n) {
+            col_ptr[j] = (int64_t)nz * cell_rptr[H];
+        } else {
+            int64_t h = j / nz;
+            int k = (int)(j - h * nz);
+            col_ptr[j] = (int64_t)nz * cell_rptr[h] + (int64_t)k * cell_cnt[h];
+        }
+    }
+    for (int64_t i = tid; i < U * nz; i += stride) {
+        int64_t e = i / nz;
+        int k = (int)(i - e * nz);
+        int h = cells[e];
+        int64_t start = cell_rptr[h];
+        row_idx[(int64_t)nz * start + (int64_t)k * cell_cnt[h] + (run_pos[e] - start)] = run_row[e];
+    }
+}
+
+// ------------------------------------------------------------- prefix sum
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER;
+
+// out[i+1] = in[0] + ... + in[i] within each tile; bsum[b] = tile total.
+template <class Tin>
+__global__ void k_scan_tiles(const Tin *__restrict__ in, int64_t n, int64_t *__restrict__ out,
+                             int64_t *__restrict__ bsum) {
+    __shared__ int64_t wsum[SCAN_THREADS / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    int64_t v[SCAN_PER];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        v[i] = base + i < n ? (int64_t)in[base + i] : 0;
+        s += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < SCAN_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < SCAN_THREADS / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    int64_t run = incl - s + (warp > 0 ? wsum[warp - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        run += v[i];
+        if (base + i < n) out[base + i + 1] = run;
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) bsum[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int64_t n, int64_t *__restrict__ out, const int64_t *__restrict__ bex) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i + 1] += bex[i / SCAN_TILE];
+}
+
+}  // namespace
+
+// Exclusive prefix sum: out[0] = 0, out[i+1] = sum of in[0..i].
+template <class Tin>
+static pdst_status scan_exclusive(const Tin *in, int64_t n, int64_t *out, cudaStream_t s) {
+    PDST_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    if (n == 0) return PDST_OK;
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    DevBuf bsum, bex;
+    PDST_TRY(bsum.alloc(sizeof(int64_t) * nb));
+    PDST_TRY(bex.alloc(sizeof(int64_t) * (nb + 1)));
+    k_scan_tiles<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, out, bsum.as<int64_t>());
+    PDST_CUDA(cudaGetLastError());
+    if (nb > 1) {
+        PDST_TRY(scan_exclusive<int64_t>(bsum.as<int64_t>(), nb, bex.as<int64_t>(), s));
+        k_scan_add<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(
+            n, out, bex.as<int64_t>());
+        PDST_CUDA(cudaGetLastError());
+    }
+    PDST_CUDA(cudaStreamSynchronize(s));   // bsum/bex are released on return
+    return PDST_OK;
+}
+
+// Host mirror of the chord count, used only to size the per-warp cell list.
+static int64_t host_chord_count(const double *c, double dx) {
+    double ax = c[2] - c[0], ay = c[3] - c[1], bx = c[4] - c[2], by = c[5] - c[3];
+    double lp = std::sqrt(ax * ax + ay * ay) + std::sqrt(bx * bx + by * by);
+    if (!(lp > 0.0)) return 0;
+    double nf = std::ceil(4.0 * lp / dx);
+    return nf < 1.0 ? 1 : (int64_t)nf;
+}
+
+static unsigned grid_for(int64_t work, int threads, int device) {
+    int64_t b = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms(device) * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int32_t *per_host,
+                              const double *kdz_host, uint32_t dtypes, cudaStream_t s) {
+    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->nz, H = h->H;
+    const double dx = h->grid.dx_km;
+    const int64_t m = h->m;
+
+    // capacity of the per-warp distinct-cell list (distinct cells <= chords)
+    int64_t maxN = 0;
+    for (int64_t r = 0; r < m; ++r) maxN = std::max(maxN, host_chord_count(ctrl_host + 6 * r, dx));
+    int64_t cap64 = std::min<int64_t>(maxN + 64, H);
+    cap64 = (cap64 + 31) / 32 * 32;
+    if (cap64 < 32) cap64 = 32;
+    const int64_t smem_budget = 200 * 1024;
+    if (cap64 * 12 > smem_budget) {
+        set_error("a ray may cross up to %lld distinct cells; the per-warp list holds %lld",
+                  (long long)cap64, (long long)(smem_budget / 12));
+        return PDST_ERR_LIMIT;
+    }
+    const int cap = (int)cap64;
+    int wpb = (int)std::min<int64_t>(8, smem_budget / (cap64 * 12));
+    size_t smem = (size_t)wpb * cap * 12;
+    PDST_CUDA(cudaFuncSetAttribute(k_count_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    PDST_CUDA(cudaFuncSetAttribute(k_fill_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+
+    DevBuf d_ctrl, d_kdz, d_cnt, d_err, d_lens, d_runrow, d_runpos;
+    PDST_TRY(d_ctrl.alloc(sizeof(double) * 6 * std::max<int64_t>(m, 1)));
+    PDST_TRY(d_kdz.alloc(sizeof(double) * (size_t)h->n_periods * nz));
+    PDST_TRY(h->row_period.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1)));
+    PDST_TRY(d_cnt.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1)));
+    PDST_TRY(d_err.alloc(sizeof(int)));
+    if (m) {
+        PDST_CUDA(cudaMemcpyAsync(d_ctrl.p, ctrl_host, sizeof(double) * 6 * m,
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(h->row_period.p, per_host, sizeof(int32_t) * m,
+                                  cudaMemcpyHostToDevice, s));
+    }
+    PDST_CUDA(cudaMemcpyAsync(d_kdz.p, kdz_host, sizeof(double) * h->n_periods * nz,
+                              cudaMemcpyHostToDevice, s));
+    PDST_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), s));
+
+    int sms = num_sms(h->device);
+    unsigned wgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + wpb - 1) / wpb,
+                                                                      (int64_t)sms * 8));
+    if (m) {
+        k_count_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx, cap,
+                                                   d_cnt.as<int32_t>(), d_err.as<int>());
+        PDST_CUDA(cudaGetLastError());
+    }
+    PDST_TRY(h->row_cptr.alloc(sizeof(int64_t) * (m + 1)));
+    PDST_TRY(scan_exclusive<int32_t>(d_cnt.as<int32_t>(), m, h->row_cptr.as<int64_t>(), s));
+    int herr = 0;
+    PDST_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaMemcpyAsync(&h->U, h->row_cptr.as<int64_t>() + m, sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("a ray crossed more distinct cells than the per-warp list holds (%d)", cap);
+        return PDST_ERR_LIMIT;
+    }
+    const int64_t U = h->U;
+    h->nnz = U * nz;
+    d_cnt.release();
+
+    PDST_TRY(h->row_cells.alloc(sizeof(int32_t) * std::max<int64_t>(U, 1)));
+    PDST_TRY(d_lens.alloc(sizeof(double) * std::max<int64_t>(U, 1)));
+    PDST_TRY(d_runrow.alloc(sizeof(int32_t) * std::max<int64_t>(U, 1)));
+    if (m) {
+        k_fill_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx, cap,
+                                                  h->row_cptr.as<int64_t>(),
+                                                  h->row_cells.as<int32_t>(), d_lens.as<double>(),
+                                                  d_runrow.as<int32_t>(), d_err.as<int>());
+        PDST_CUDA(cudaGetLastError());
+    }
+
+    // values in CSR order
+    const int64_t nnz = h->nnz;
+    for (int d = 0; d < 3; ++d) {
+        if (!(dtypes & (1u << d))) continue;
+        size_t es = d == PDST_F64 ? 8 : d == PDST_F32 ? 4 : 2;
+        PDST_TRY(h->vals[d].csr.alloc(es * std::max<int64_t>(nnz, 1)));
+        PDST_TRY(h->vals[d].csc.alloc(es * std::max<int64_t>(nnz, 1)));
+        h->vals[d].present = true;
+    }
+    if (nnz) {
+        k_expand_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
+            U, nz, d_lens.as<double>(), d_runrow.as<int32_t>(), h->row_period.as<int32_t>(),
+            d_kdz.as<double>(), h->vals[0].present ? h->vals[0].csr.as<double>() : nullptr,
+            h->vals[1].present ? h->vals[1].csr.as<float>() : nullptr,
+            h->vals[2].present ? h->vals[2].csr.as<__nv_bfloat16>() : nullptr);
+        PDST_CUDA(cudaGetLastError());
+    }
+
+    // cell-level transpose
+    PDST_TRY(h->cell_cnt.alloc(sizeof(int32_t) * H));
+    PDST_TRY(h->cell_rptr.alloc(sizeof(int64_t) * (H + 1)));
+    PDST_TRY(h->cell_rows.alloc(sizeof(int32_t) * std::max<int64_t>(U, 1)));
+    PDST_TRY(d_runpos.alloc(sizeof(int64_t) * std::max<int64_t>(U, 1)));
+    PDST_CUDA(cudaMemsetAsync(h->cell_cnt.p, 0, sizeof(int32_t) * H, s));
+    if (U) {
+        k_cell_count<<<grid_for(U, 256, h->device), 256, 0, s>>>(U, h->row_cells.as<int32_t>(),
+                                                                 h->cell_cnt.as<int32_t>());
+        PDST_CUDA(cudaGetLastError());
+    }
+    PDST_TRY(scan_exclusive<int32_t>(h->cell_cnt.as<int32_t>(), H, h->cell_rptr.as<int64_t>(), s));
+    if (U) {
+        const int ch = 256;
+        int64_t nchunk = (m + ch - 1) / ch;
+        DevBuf ccnt, cbase;
+        PDST_TRY(ccnt.alloc(sizeof(int32_t) * nchunk * H));
+        PDST_TRY(cbase.alloc(sizeof(int64_t) * nchunk * H));
+        PDST_CUDA(cudaMemsetAsync(ccnt.p, 0, sizeof(int32_t) * nchunk * H, s));
+        k_chunk_count<<<grid_for(U, 256, h->device), 256, 0, s>>>(
+            U, ch, H, h->row_cells.as<int32_t>(), d_runrow.as<int32_t>(), ccnt.as<int32_t>());
+        PDST_CUDA(cudaGetLastError());
+        k_chunk_scan<<<(H + 127) / 128, 128, 0, s>>>(nchunk, H, h->cell_rptr.as<int64_t>(),
+                                                      ccnt.as<int32_t>(), cbase.as<int64_t>());
+        PDST_CUDA(cudaGetLastError());
+        k_chunk_place<<<(unsigned)nchunk, 128, 0, s>>>(m, ch, H, h->row_cptr.as<int64_t>(),
+                                                       h->row_cells.as<int32_t>(),
+                                                       cbase.as<int64_t>(),
+                                                       h->cell_rows.as<int32_t>(),
+                                                       d_runpos.as<int64_t>());
+        PDST_CUDA(cudaGetLastError());
+        unsigned g = grid_for(nnz, 256, h->device);
+        if (h->vals[0].present)
+            k_csc_values<double><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(),
+                                                  d_runpos.as<int64_t>(), h->cell_rptr.as<int64_t>(),
+                                                  h->cell_cnt.as<int32_t>(),
+                                                  h->vals[0].csr.as<double>(),
+                                                  h->vals[0].csc.as<double>());
+        if (h->vals[1].present)
+            k_csc_values<float><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(),
+                                                 d_runpos.as<int64_t>(), h->cell_rptr.as<int64_t>(),
+                                                 h->cell_cnt.as<int32_t>(),
+                                                 h->vals[1].csr.as<float>(),
+                                                 h->vals[1].csc.as<float>());
+        if (h->vals[2].present)
+            k_csc_values<__nv_bfloat16><<<g, 256, 0, s>>>(
+                U, nz, h->row_cells.as<int32_t>(), d_runpos.as<int64_t>(),
+                h->cell_rptr.as<int64_t>(), h->cell_cnt.as<int32_t>(),
+                h->vals[2].csr.as<__nv_bfloat16>(), h->vals[2].csc.as<__nv_bfloat16>());
+        PDST_CUDA(cudaGetLastError());
+        PDST_CUDA(cudaStreamSynchronize(s));   // chunk tables are released on scope exit
+    }
+
+    if (h->formats & (1u << PDST_FMT_ELEMENT)) {
+        PDST_TRY(h->row_ptr.alloc(sizeof(int64_t) * (m + 1)));
+        PDST_TRY(h->col.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+        PDST_TRY(h->col_ptr.alloc(sizeof(int64_t) * ((int64_t)h->n + 1)));
+        PDST_TRY(h->row_idx.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+        k_elem_csr<<<grid_for(std::max<int64_t>(nnz, m + 1), 256, h->device), 256, 0, s>>>(
+            m, U, nz, h->row_cptr.as<int64_t>(), h->row_cells.as<int32_t>(),
+            h->row_ptr.as<int64_t>(), h->col.as<int32_t>());
+        PDST_CUDA(cudaGetLastError());
+        k_elem_csc<<<grid_for(std::max<int64_t>(nnz, (int64_t)h->n + 1), 256, h->device), 256, 0,
+                     s>>>(U, H, nz, h->row_cells.as<int32_t>(), d_runrow.as<int32_t>(),
+                          d_runpos.as<int64_t>(), h->cell_rptr.as<int64_t>(),
+                          h->cell_cnt.as<int32_t>(), h->col_ptr.as<int64_t>(),
+                          h->row_idx.as<int32_t>());
+        PDST_CUDA(cudaGetLastError());
+    }
+    PDST_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("G assembly: per-row cell list inconsistent between passes (code %d)", herr);
+        return PDST_ERR_CUDA;
+    }
+    return PDST_OK;
+}
+
+}  // namespace pdst
+
+using namespace pdst;
+
+extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
+                                    const double *ctrl_host, const int32_t *path_period_host,
+                                    int32_t n_periods, const double *kdz_host,
+                                    const pdst_build_opts *opts, void *stream,
+                                    pdst_handle_t *out) {
+    PDST_CHECK_ARG(out != nullptr, "pdst_build_G: out is NULL");
+    *out = nullptr;
+    PDST_CHECK_ARG(grid != nullptr, "pdst_build_G: grid is NULL");
+    PDST_CHECK_ARG(grid->nx > 0 && grid->ny > 0 && grid->nz > 0,
+                   "pdst_build_G: grid dimensions must be positive");
+    PDST_CHECK_ARG(std::isfinite(grid->dx_km) && grid->dx_km > 0.0,
+                   "pdst_build_G: dx_km must be positive and finite");
+    PDST_CHECK_ARG(n_paths >= 0 && n_paths < INT32_MAX, "pdst_build_G: n_paths out of range");
+    PDST_CHECK_ARG(n_periods > 0, "pdst_build_G: n_periods must be positive");
+    PDST_CHECK_ARG(kdz_host != nullptr, "pdst_build_G: kdz is NULL");
+    PDST_CHECK_ARG(n_paths == 0 || (ctrl_host && path_period_host),
+                   "pdst_build_G: ctrl / path_period is NULL");
+    int64_t H = (int64_t)grid->nx * grid->ny, n = H * grid->nz;
+    PDST_CHECK_ARG(n < INT32_MAX, "pdst_build_G: nx*ny*nz must fit in int32");
+    for (int64_t i = 0; i < 6 * n_paths; ++i)
+        PDST_CHECK_ARG(std::isfinite(ctrl_host[i]), "pdst_build_G: non-finite ray coordinate %lld",
+                       (long long)i);
+    for (int64_t r = 0; r < n_paths; ++r)
+        PDST_CHECK_ARG(path_period_host[r] >= 0 && path_period_host[r] < n_periods,
+                       "pdst_build_G: period index of path %lld out of range", (long long)r);
+    for (int64_t i = 0; i < (int64_t)n_periods * grid->nz; ++i)
+        PDST_CHECK_ARG(std::isfinite(kdz_host[i]), "pdst_build_G: non-finite kdz entry");
+    uint32_t dtypes = opts && opts->value_dtypes ? opts->value_dtypes
+                                                 : (1u << PDST_F64) | (1u << PDST_F32);
+    uint32_t formats = opts && opts->formats ? opts->formats
+                                             : (1u << PDST_FMT_ELEMENT) | (1u << PDST_FMT_BLOCKED);
+    PDST_CHECK_ARG((dtypes & ~7u) == 0, "pdst_build_G: unknown value dtype bits");
+    PDST_CHECK_ARG((formats & ~3u) == 0, "pdst_build_G: unknown format bits");
+
+    pdst_handle *h = new pdst_handle();
+    cudaGetDevice(&h->device);
+    h->grid = *grid;
+    h->m = n_paths;
+    h->n = (int32_t)n;
+    h->H = (int32_t)H;
+    h->nz = grid->nz;
+    h->n_periods = n_periods;
+    h->formats = formats;
+    pdst_status st = build_impl(h, ctrl_host, path_period_host, kdz_host, dtypes,
+                                (cudaStream_t)stream);
+    if (st != PDST_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PDST_OK;
+}

@@ -1,0 +1,167 @@
+// common.cuh -- internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/pdst.h"
+
+namespace pdst {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+
+// Evaluate a CUDA call; on failure record the message and return the status.
+#define PDST_CUDA(call)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            ::pdst::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,             \
+                              cudaGetErrorString(e_));                               \
+            return e_ == cudaErrorMemoryAllocation ? PDST_ERR_OOM : PDST_ERR_CUDA;   \
+        }                                                                            \
+    } while (0)
+
+#define PDST_TRY(expr)                                                               \
+    do {                                                                             \
+        pdst_status s_ = (expr);                                                     \
+        if (s_ != PDST_OK) return s_;                                                \
+    } while (0)
+
+#define PDST_CHECK_ARG(cond, ...)                                                    \
+    do {                                                                             \
+        if (!(cond)) {                                                               \
+            ::pdst::set_error(__VA_ARGS__);                                          \
+            return PDST_ERR_ARG;                                                     \
+        }                                                                            \
+    } while (0)
+
+// ------------------------------------------------------------ device memory
+
+// Owning device buffer (cudaMalloc / cudaFree).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    pdst_status alloc(size_t nbytes) {
+        if (p && bytes >= nbytes) return PDST_OK;
+        release();
+        if (nbytes == 0) nbytes = 16;
+        cudaError_t e = cudaMalloc(&p, nbytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            set_error("cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? PDST_ERR_OOM : PDST_ERR_CUDA;
+        }
+        bytes = nbytes;
+        return PDST_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------- LSQR state
+
+// Scalars of one LSQR recurrence (Paige & Saunders 1982 notation), kept in
+// device memory and advanced by the last block of the adjoint kernel.
+struct LsqrScalars {
+    double alpha, beta;            // alpha_i (||v-bar||) and beta (||u-bar||)
+    double rhobar, phibar;
+    double anorm, acond, ddnorm, res2, xnorm, xxnorm, z, cs2, sn2;
+    double rnorm, arnorm, bnorm;
+    double t1, t2;                 // pending update x += t1 w, w = v + t2 w
+    double wnorm2;                 // ||w||^2 of the current w
+    double damp, atol, btol, ctol;
+    double w_smooth;               // smoothing weight w
+    double lam_rows;               // lambda of the appended lambda*D rows (scaled form)
+    double *hist;                  // optional ||r|| history (device)
+    int32_t itn, itmax, istop, pending, done, err;
+};
+
+// "Last block" counters of the reduction kernels.
+struct LsqrSync {
+    unsigned int count[8];
+};
+
+struct ValueSet {
+    DevBuf csr;   // values in CSR order (row-major, cells ascending, depth fastest)
+    DevBuf csc;   // values in CSC order (column-major, rows ascending)
+    bool present = false;
+};
+
+struct LsqrWork;   // lsqr.cu
+
+void destroy_work(LsqrWork *w);
+
+inline int num_sms(int device) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    return v > 0 ? v : 148;
+}
+
+}  // namespace pdst
+
+struct pdst_handle {
+    int device = 0;
+    pdst_grid grid{};
+    int64_t m = 0;          // rows of G
+    int32_t n = 0;          // columns
+    int32_t H = 0;          // horizontal cells nx*ny
+    int32_t nz = 0;
+    int64_t U = 0;          // (row, cell) runs = nnz / nz
+    int64_t nnz = 0;
+    int32_t n_periods = 0;
+    uint32_t formats = 0;
+
+    pdst::DevBuf row_period;   // int32 [m]
+    // blocked (cell-level) indices, always built
+    pdst::DevBuf row_cptr;     // int64 [m+1]  run pointer per row
+    pdst::DevBuf row_cells;    // int32 [U]    cell of each run (ascending in a row)
+    pdst::DevBuf cell_rptr;    // int64 [H+1]  run pointer per cell (transpose)
+    pdst::DevBuf cell_rows;    // int32 [U]    rows of each cell (ascending)
+    pdst::DevBuf cell_cnt;     // int32 [H]    rows per cell
+    // element indices (PDST_FMT_ELEMENT)
+    pdst::DevBuf row_ptr;      // int64 [m+1]
+    pdst::DevBuf col;          // int32 [nnz]
+    pdst::DevBuf col_ptr;      // int64 [n+1]
+    pdst::DevBuf row_idx;      // int32 [nnz]
+    pdst::ValueSet vals[3];    // by pdst_dtype
+
+    pdst::DevBuf colscale;     // double [n] right diagonal scaling D
+    bool has_colscale = false;
+
+    pdst::LsqrWork *work = nullptr;
+    ~pdst_handle() { pdst::destroy_work(work); }
+};
+
+// ----------------------------------------------------------- device helpers
+
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T> __device__ __forceinline__ T cvt(double v);
+template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt<float>(double v) { return (float)v; }
+
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }

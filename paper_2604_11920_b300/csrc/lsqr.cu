@@ -1,0 +1,944 @@
+// lsqr.cu -- LSQR (Paige & Saunders 1982) on the augmented operator
+// A = [G; w L] (or [G D; w L D; lambda D] with a right diagonal scaling),
+// the solver of the paper's least-squares module ("Solver for the
+// Large-scale Linear System"; the paper names LSQR beside LSMR).
+//
+// One iteration is three kernels:
+//   k_fwd  u-bar <- A v - alpha u and beta = ||u-bar||   (G rows: warp per CSR
+//          row, gather of v; L rows: 7-point stencil, thread per column)
+//   k_adj  v-bar <- A^T u - beta v and alpha = ||v-bar|| (warp per CSC column,
+//          gather of u; the stencil term added by the same warp); the last
+//          block to finish advances the FP64 scalar recurrence (rotations,
+//          norm estimates, stopping rules)
+//   k_upd  x += t1 w, w = v + t2 w in FP64 and ||w||^2
+// Both products are gathers (no atomics).  Vectors are never normalised in
+// place: u-bar and v-bar are kept with their norms and the 1/beta, 1/alpha
+// factors are folded into the next product, so each Golub-Kahan step is one
+// sweep plus one fused norm reduction.  Every reduction is a fixed-order
+// block sum followed by a fixed-order sum over blocks done by the last block,
+// so results are bit-reproducible run to run.  The iteration is replayed from
+// a CUDA graph; kernels return at entry once the stopping rule has fired.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pdst {
+
+constexpr int LT = 256;         // threads per block of the LSQR kernels
+constexpr int MAXBLK = 4096;    // upper bound on blocks per reduction kernel
+
+enum { FMT_ELEM = 0, FMT_BLK = 1 };
+
+template <class VT, class ST> struct OpArgs {
+    int64_t m;
+    int32_t n;
+    int nx, ny, nz;
+    const int64_t *row_ptr;   // element CSR
+    const int32_t *col;
+    const int64_t *col_ptr;   // element CSC
+    const int32_t *row_idx;
+    const int64_t *row_cptr;  // blocked
+    const int32_t *row_cells;
+    const int64_t *cell_rptr;
+    const int32_t *cell_rows;
+    const int32_t *cell_cnt;
+    const VT *val;            // CSR order
+    const VT *valT;           // CSC order
+    const double *D;          // right diagonal scaling or nullptr
+    int lam_rows_on;          // append lambda*D rows
+    ST *ubar;                 // M = m + n (+ n)
+    ST *vbar;                 // n
+    ST *vsc;                  // n: D o v-bar (== vbar when no scaling)
+    double *x, *wv;           // n, FP64
+    double *partial;          // 3 x MAXBLK
+    LsqrScalars *sc;
+    LsqrSync *sy;
+};
+
+// ------------------------------------------------------------ load helpers
+
+template <class VT> struct Pack4;
+template <> struct Pack4<float> {
+    static __device__ __forceinline__ void ld(const float *p, float v[4]) {
+        float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct Pack4<double> {
+    static __device__ __forceinline__ void ld(const double *p, double v[4]) {
+        double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <> struct Pack4<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float v[4]) {
+        uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
+    }
+};
+template <class VT> struct Wide { using T = VT; };
+template <> struct Wide<__nv_bfloat16> { using T = float; };
+
+template <class ST> __device__ __forceinline__ void ldx4(const ST *p, ST v[4]);
+template <> __device__ __forceinline__ void ldx4<float>(const float *p, float v[4]) {
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <> __device__ __forceinline__ void ldx4<double>(const double *p, double v[4]) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ float ldval(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ double ldval(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ldval(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+
+// ------------------------------------------------------------ dot products
+
+// sum_p val[p] * x[idx[p]] over p in [ptr[r], ptr[r+1]) by one warp: ragged
+// head and tail by single lanes, the aligned body four entries per lane with
+// 128-bit index loads and streaming (evict-first) value loads.
+template <class VT, class AT, class XT>
+__device__ __forceinline__ AT dot_elem(const int64_t *__restrict__ ptr,
+                                       const int32_t *__restrict__ idx,
+                                       const VT *__restrict__ val, const XT *__restrict__ x,
+                                       int64_t r, int lane) {
+    const int64_t p0 = ptr[r], p1 = ptr[r + 1];
+    int64_t a = (p0 + 3) & ~int64_t(3);
+    if (a > p1) a = p1;
+    const int64_t b = a + ((p1 - a) & ~int64_t(3));
+    AT s = 0;
+    if (p0 + lane < a) s += (AT)widen(val[p0 + lane]) * (AT)__ldg(x + idx[p0 + lane]);
+    for (int64_t p = a + 4 * lane; p < b; p += 128) {
+        int4 c = __ldcs(reinterpret_cast<const int4 *>(idx + p));
+        typename Wide<VT>::T v[4];
+        Pack4<VT>::ld(val + p, v);
+        s += (AT)v[0] * (AT)__ldg(x + c.x);
+        s += (AT)v[1] * (AT)__ldg(x + c.y);
+        s += (AT)v[2] * (AT)__ldg(x + c.z);
+        s += (AT)v[3] * (AT)__ldg(x + c.w);
+    }
+    if (b + lane < p1) s += (AT)widen(val[b + lane]) * (AT)__ldg(x + idx[b + lane]);
+    return warp_sum(s);
+}
+
+// Blocked CSR row: runs e in [row_cptr[r], row_cptr[r+1]) of nz consecutive
+// columns cells[e]*nz + k, values val[nz*e + k].  With nz % 4 == 0 every group
+// of four entries lies in one run and gathers a contiguous 4-vector of x.
+template <class VT, class AT, class XT>
+__device__ __forceinline__ AT dot_blk_row(const int64_t *__restrict__ row_cptr,
+                                          const int32_t *__restrict__ cells,
+                                          const VT *__restrict__ val, const XT *__restrict__ x,
+                                          int64_t r, int nz, int lane) {
+    const int64_t e0 = row_cptr[r], e1 = row_cptr[r + 1];
+    const int64_t p0 = e0 * nz;
+    const uint32_t len = (uint32_t)((e1 - e0) * nz);
+    AT s = 0;
+    if ((nz & 3) == 0) {
+        for (uint32_t rel = 4u * lane; rel < len; rel += 128u) {
+            uint32_t ee = rel / (uint32_t)nz;
+            uint32_t k = rel - ee * (uint32_t)nz;
+            int h = __ldg(cells + e0 + ee);
+            typename Wide<VT>::T v[4];
+            Pack4<VT>::ld(val + p0 + rel, v);
+            XT xv[4];
+            ldx4<XT>(x + (int64_t)h * nz + k, xv);
+            s += (AT)v[0] * (AT)xv[0];
+            s += (AT)v[1] * (AT)xv[1];
+            s += (AT)v[2] * (AT)xv[2];
+            s += (AT)v[3] * (AT)xv[3];
+        }
+    } else {
+        for (uint32_t rel = lane; rel < len; rel += 32u) {
+            uint32_t ee = rel / (uint32_t)nz;
+            uint32_t k = rel - ee * (uint32_t)nz;
+            int h = __ldg(cells + e0 + ee);
+            s += (AT)widen(val[p0 + rel]) * (AT)__ldg(x + (int64_t)h * nz + k);
+        }
+    }
+    return warp_sum(s);
+}
+
+// Blocked CSC column j = h*nz + k: rows cell_rows[cell_rptr[h] + q] shared by
+// the nz columns of the cell, values valT[nz*cell_rptr[h] + k*cnt[h] + q].
+template <class VT, class AT, class XT>
+__device__ __forceinline__ AT dot_blk_col(const int64_t *__restrict__ cell_rptr,
+                                          const int32_t *__restrict__ cell_cnt,
+                                          const int32_t *__restrict__ cell_rows,
+                                          const VT *__restrict__ valT, const XT *__restrict__ u,
+                                          int64_t j, int nz, int lane) {
+    const int64_t h = j / nz;
+    const int k = (int)(j - h * nz);
+    const int64_t c0 = cell_rptr[h];
+    const int cnt = cell_cnt[h];
+    const VT *v = valT + (int64_t)nz * c0 + (int64_t)k * cnt;
+    const int32_t *rows = cell_rows + c0;
+    AT s0 = 0, s1 = 0;
+    int q = lane;
+    for (; q + 32 < cnt; q += 64) {
+        AT a0 = (AT)ldval(v + q), a1 = (AT)ldval(v + q + 32);
+        int r0 = __ldg(rows + q), r1 = __ldg(rows + q + 32);
+        s0 += a0 * (AT)__ldg(u + r0);
+        s1 += a1 * (AT)__ldg(u + r1);
+    }
+    if (q < cnt) s0 += (AT)ldval(v + q) * (AT)__ldg(u + __ldg(rows + q));
+    return warp_sum(s0 + s1);
+}
+
+// (L x)_j = sum over existing 7-point neighbours i of (x_j - x_i).
+template <class AT, class XT>
+__device__ __forceinline__ AT laplace(const XT *__restrict__ x, int64_t j, int nx, int ny, int nz) {
+    const int k = (int)(j % nz);
+    const int64_t hh = j / nz;
+    const int ix = (int)(hh % nx), iy = (int)(hh / nx);
+    const int64_t sy = (int64_t)nx * nz;
+    const AT c = (AT)x[j];
+    AT s = 0;
+    if (k > 0) s += c - (AT)x[j - 1];
+    if (k < nz - 1) s += c - (AT)x[j + 1];
+    if (ix > 0) s += c - (AT)x[j - nz];
+    if (ix < nx - 1) s += c - (AT)x[j + nz];
+    if (iy > 0) s += c - (AT)x[j - sy];
+    if (iy < ny - 1) s += c - (AT)x[j + sy];
+    return s;
+}
+
+// ------------------------------------------------------------- reductions
+
+// Block sum of v, then the block that finishes last sums the per-block
+// partials in index order.  Returns true in that block; `total` is valid in
+// its first warp.
+__device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigned *counter,
+                                              double &total) {
+    __shared__ double red[LT / 32];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+        partial[blockIdx.x] = b;
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double s = 0.0;
+    if (warp == 0) {
+        for (int i = lane; i < (int)gridDim.x; i += 32) s += __ldcg(partial + i);
+        s = warp_sum(s);
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    total = s;
+    return true;
+}
+
+// One LSQR step of the scalar recurrence (Paige & Saunders 1982): damping
+// rotation, plane rotation, x/w update coefficients, norm estimates and
+// stopping rules.  alpha_new = ||v-bar_{i+1}||, sc->beta = beta_{i+1},
+// sc->alpha = alpha_i, sc->wnorm2 = ||w_i||^2.
+__device__ void lsqr_step(LsqrScalars *sc, double alpha_new) {
+    const double alpha = sc->alpha, beta = sc->beta, damp = sc->damp;
+    const double dampsq = damp * damp;
+    if (beta > 0.0)
+        sc->anorm = sqrt(sc->anorm * sc->anorm + alpha * alpha + beta * beta + dampsq);
+    else
+        alpha_new = alpha;
+    double rhobar = sc->rhobar, phibar = sc->phibar, rhobar1 = rhobar, psi = 0.0;
+    if (damp > 0.0) {
+        rhobar1 = sqrt(rhobar * rhobar + dampsq);
+        const double cs1 = rhobar / rhobar1, sn1 = damp / rhobar1;
+        psi = sn1 * phibar;
+        phibar = cs1 * phibar;
+    }
+    const double rho = sqrt(rhobar1 * rhobar1 + beta * beta);
+    if (!(rho > 0.0) || !isfinite(rho)) {
+        sc->err = 1;
+        sc->done = 1;
+        return;
+    }
+    const double cs = rhobar1 / rho, sn = beta / rho;
+    const double theta = sn * alpha_new;
+    sc->rhobar = -cs * alpha_new;
+    const double phi = cs * phibar;
+    phibar = sn * phibar;
+    sc->phibar = phibar;
+    const double tau = sn * phi;
+    sc->t1 = phi / rho;
+    sc->t2 = -theta / rho;
+    sc->ddnorm += sc->wnorm2 / (rho * rho);
+    // ||x|| estimate from the LQ factors of the upper bidiagonal R_k
+    const double delta = sc->sn2 * rho, gambar = -sc->cs2 * rho;
+    const double rhs = phi - delta * sc->z;
+    const double zbar = rhs / gambar;
+    sc->xnorm = sqrt(sc->xxnorm + zbar * zbar);
+    const double gamma = sqrt(gambar * gambar + theta * theta);
+    sc->cs2 = gambar / gamma;
+    sc->sn2 = theta / gamma;
+    sc->z = rhs / gamma;
+    sc->xxnorm += sc->z * sc->z;
+    sc->acond = sc->anorm * sqrt(sc->ddnorm);
+    sc->res2 += psi * psi;
+    sc->rnorm = sqrt(phibar * phibar + sc->res2);
+    sc->arnorm = alpha_new * fabs(tau);
+    sc->alpha = alpha_new;
+    sc->itn += 1;
+    sc->pending = 1;
+    if (sc->hist) sc->hist[sc->itn - 1] = sc->rnorm;
+
+    const double eps = DBL_EPSILON;
+    const double bnorm = sc->bnorm, anorm = sc->anorm, xnorm = sc->xnorm, rnorm = sc->rnorm;
+    const double test1 = rnorm / bnorm;
+    const double test2 = sc->arnorm / (anorm * rnorm + eps);
+    const double test3 = 1.0 / (sc->acond + eps);
+    const double t1s = test1 / (1.0 + anorm * xnorm / bnorm);
+    const double rtol = sc->btol + sc->atol * anorm * xnorm / bnorm;
+    int istop = 0;
+    if (test1 <= rtol) istop = 1;
+    else if (test2 <= sc->atol) istop = 2;
+    else if (test3 <= sc->ctol) istop = 3;
+    else if (1.0 + t1s <= 1.0) istop = 4;
+    else if (1.0 + test2 <= 1.0) istop = 5;
+    else if (1.0 + test3 <= 1.0) istop = 6;
+    else if (sc->itn >= sc->itmax) istop = 7;
+    sc->istop = istop;
+    if (!isfinite(rnorm) || !isfinite(sc->arnorm) || !isfinite(sc->t1) || !isfinite(sc->t2)) {
+        sc->err = 1;
+        sc->done = 1;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+
+// beta_1 u_1 = [d; 0]: u-bar = [d; 0], beta_1 = ||d||, x = 0.
+template <class ST>
+__global__ void __launch_bounds__(LT) k_init(int64_t m, int64_t M, int32_t n,
+                                             const double *__restrict__ d, ST *ubar, double *x,
+                                             double *wv, double *partial, LsqrScalars *sc,
+                                             LsqrSync *sy) {
+    double ss = 0.0;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = t0; i < M; i += st) {
+        double v = i < m ? d[i] : 0.0;
+        ubar[i] = (ST)v;
+        ss += v * v;
+    }
+    for (int64_t j = t0; j < n; j += st) {
+        x[j] = 0.0;
+        wv[j] = 0.0;
+    }
+    double tot;
+    if (grid_sum_last(ss, partial, &sy->count[0], tot) && threadIdx.x == 0) {
+        const double b = sqrt(tot);
+        sc->beta = b;
+        sc->bnorm = b;
+        sc->rnorm = b;
+        sc->phibar = b;
+        if (!isfinite(b)) sc->err = 1;
+        if (!(b > 0.0) || !isfinite(b)) sc->done = 1;
+    }
+}
+
+// u-bar <- (A v-bar)/alpha - (alpha/beta) u-bar;  beta <- ||u-bar||.
+template <class VT, class ST, int FMT>
+__global__ void __launch_bounds__(LT) k_fwd(OpArgs<VT, ST> a) {
+    LsqrScalars *sc = a.sc;
+    if (sc->done | sc->istop) return;
+    using AT = ST;
+    const double alpha = sc->alpha, beta = sc->beta;
+    const AT ia = alpha > 0.0 ? (AT)(1.0 / alpha) : (AT)0;
+    const AT cu = beta > 0.0 ? (AT)(alpha / beta) : (AT)0;
+    const AT wsm = (AT)sc->w_smooth, lamr = (AT)sc->lam_rows;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double ss = 0.0;
+    for (int64_t r = gw; r < a.m; r += nw) {
+        AT dot = FMT == FMT_ELEM
+                     ? dot_elem<VT, AT, ST>(a.row_ptr, a.col, a.val, a.vsc, r, lane)
+                     : dot_blk_row<VT, AT, ST>(a.row_cptr, a.row_cells, a.val, a.vsc, r, a.nz, lane);
+        if (lane == 0) {
+            AT u = dot * ia - cu * a.ubar[r];
+            a.ubar[r] = u;
+            ss += (double)u * (double)u;
+        }
+    }
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = t0; j < a.n; j += st) {
+        AT lap = laplace<AT, ST>(a.vsc, j, a.nx, a.ny, a.nz);
+        ST *ur = a.ubar + a.m + j;
+        AT u = wsm * lap * ia - cu * *ur;
+        *ur = u;
+        ss += (double)u * (double)u;
+        if (a.lam_rows_on) {
+            ST *ul = a.ubar + a.m + a.n + j;
+            AT u2 = lamr * (AT)a.vsc[j] * ia - cu * *ul;
+            *ul = u2;
+            ss += (double)u2 * (double)u2;
+        }
+    }
+    double tot;
+    if (grid_sum_last(ss, a.partial, &a.sy->count[1], tot) && threadIdx.x == 0) {
+        const double b = sqrt(tot);
+        if (!isfinite(b)) {
+            sc->err = 1;
+            sc->done = 1;
+        }
+        sc->beta = b;
+    }
+}
+
+// v-bar <- (A^T u-bar)/beta - (beta/alpha) v-bar;  alpha <- ||v-bar||, then
+// the scalar recurrence (or its initialisation when init != 0).
+template <class VT, class ST, int FMT>
+__global__ void __launch_bounds__(LT) k_adj(OpArgs<VT, ST> a, int init) {
+    LsqrScalars *sc = a.sc;
+    if (sc->done | sc->istop) return;
+    using AT = ST;
+    const double alpha = sc->alpha, beta = sc->beta;
+    const bool skip = !init && !(beta > 0.0);
+    const AT ib = beta > 0.0 ? (AT)(1.0 / beta) : (AT)0;
+    const AT cv = init ? (AT)0 : (alpha > 0.0 ? (AT)(beta / alpha) : (AT)0);
+    const AT wsm = (AT)sc->w_smooth, lamr = (AT)sc->lam_rows;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double ss = 0.0;
+    if (!skip) {
+        for (int64_t j = gw; j < a.n; j += nw) {
+            AT dot = FMT == FMT_ELEM
+                         ? dot_elem<VT, AT, ST>(a.col_ptr, a.row_idx, a.valT, a.ubar, j, lane)
+                         : dot_blk_col<VT, AT, ST>(a.cell_rptr, a.cell_cnt, a.cell_rows, a.valT,
+                                                   a.ubar, j, a.nz, lane);
+            if (lane == 0) {
+                AT s = dot + wsm * laplace<AT, ST>(a.ubar + a.m, j, a.nx, a.ny, a.nz);
+                if (a.lam_rows_on) s += lamr * (AT)a.ubar[a.m + a.n + j];
+                AT dj = a.D ? (AT)a.D[j] : (AT)1;
+                s *= dj;
+                AT v = s * ib - cv * a.vbar[j];
+                a.vbar[j] = v;
+                if (a.D) a.vsc[j] = dj * v;
+                ss += (double)v * (double)v;
+            }
+        }
+    }
+    double tot;
+    if (grid_sum_last(ss, a.partial + MAXBLK, &a.sy->count[2], tot) && threadIdx.x == 0) {
+        double an = skip ? alpha : sqrt(tot);
+        if (!isfinite(an)) {
+            sc->err = 1;
+            sc->done = 1;
+            return;
+        }
+        if (init) {
+            sc->alpha = an;
+            sc->rhobar = an;
+            sc->arnorm = an * beta;
+            sc->pending = 2;
+            if (!(sc->arnorm > 0.0)) sc->done = 1;
+        } else {
+            lsqr_step(sc, an);
+        }
+    }
+}
+
+// x += t1 w; w = v + t2 w (FP64), v = v-bar/alpha;  ||w||^2.
+template <class ST>
+__global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vbar, double *x,
+                                            double *wv, double *partial, LsqrScalars *sc,
+                                            LsqrSync *sy) {
+    const int pend = sc->pending;
+    if (!pend) return;
+    const double alpha = sc->alpha;
+    const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    const double t1 = sc->t1, t2 = sc->t2;
+    double ss = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)vbar[j] * ia;
+        double w = wv[j];
+        if (pend == 2) {
+            w = v;
+        } else {
+            x[j] += t1 * w;
+            w = v + t2 * w;
+        }
+        wv[j] = w;
+        ss += w * w;
+    }
+    double tot;
+    if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot) && threadIdx.x == 0) {
+        sc->wnorm2 = tot;
+        sc->pending = 0;
+    }
+}
+
+__global__ void k_finalize(int32_t n, const double *__restrict__ x, const double *__restrict__ D,
+                           double *m_out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        m_out[j] = D ? D[j] * x[j] : x[j];
+}
+
+// y = G x or G^T x with FP64 vectors (pdst_apply_G).
+template <class VT, int FMT>
+__global__ void __launch_bounds__(LT) k_spmv(OpArgs<VT, double> a, int trans,
+                                             const double *__restrict__ xin, double *y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t rows = trans ? a.n : a.m;
+    for (int64_t r = gw; r < rows; r += nw) {
+        double s;
+        if (!trans)
+            s = FMT == FMT_ELEM ? dot_elem<VT, double, double>(a.row_ptr, a.col, a.val, xin, r, lane)
+                                : dot_blk_row<VT, double, double>(a.row_cptr, a.row_cells, a.val,
+                                                                  xin, r, a.nz, lane);
+        else
+            s = FMT == FMT_ELEM
+                    ? dot_elem<VT, double, double>(a.col_ptr, a.row_idx, a.valT, xin, r, lane)
+                    : dot_blk_col<VT, double, double>(a.cell_rptr, a.cell_cnt, a.cell_rows,
+                                                      a.valT, xin, r, a.nz, lane);
+        if (lane == 0) y[r] = s;
+    }
+}
+
+// ||[G; w L; lam I]_{:,j}||^2 -> D_j = 1/sqrt(.)  (column-norm scaling).
+template <class VT>
+__global__ void __launch_bounds__(LT) k_colnorm_scale(OpArgs<VT, double> a, double w, double lam,
+                                                      double *D) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = gw; j < a.n; j += nw) {
+        const int64_t h = j / a.nz;
+        const int k = (int)(j - h * a.nz);
+        const int64_t c0 = a.cell_rptr[h];
+        const int cnt = a.cell_cnt[h];
+        const VT *v = a.valT + (int64_t)a.nz * c0 + (int64_t)k * cnt;
+        double s = 0.0;
+        for (int q = lane; q < cnt; q += 32) {
+            double t = (double)widen(v[q]);
+            s += t * t;
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+            const int ix = (int)(h % a.nx), iy = (int)(h / a.nx);
+            const int deg = (k > 0) + (k < a.nz - 1) + (ix > 0) + (ix < a.nx - 1) + (iy > 0) +
+                            (iy < a.ny - 1);
+            const double c = s + w * w * ((double)deg * deg + deg) + lam * lam;
+            D[j] = c > 0.0 ? 1.0 / sqrt(c) : 1.0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- driver
+
+struct LsqrWork {
+    int dtype = -1, format = -1, lamrows = -1;
+    const void *graph_D = nullptr;
+    int64_t M = 0;
+    DevBuf ubar, vbar, vsc, x, wv, partial, scal, sync;
+    LsqrScalars *h_scal = nullptr;   // pinned
+    unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
+    std::map<int, cudaGraphExec_t> graphs;   // key: kblock
+    ~LsqrWork() {
+        for (auto &g : graphs)
+            if (g.second) cudaGraphExecDestroy(g.second);
+        if (h_scal) cudaFreeHost(h_scal);
+    }
+};
+
+void destroy_work(LsqrWork *w) { delete w; }
+
+template <class VT, class ST>
+static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool scaled, bool lamrows) {
+    OpArgs<VT, ST> a{};
+    a.m = h->m;
+    a.n = h->n;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.nz = h->nz;
+    a.row_ptr = h->row_ptr.as<int64_t>();
+    a.col = h->col.as<int32_t>();
+    a.col_ptr = h->col_ptr.as<int64_t>();
+    a.row_idx = h->row_idx.as<int32_t>();
+    a.row_cptr = h->row_cptr.as<int64_t>();
+    a.row_cells = h->row_cells.as<int32_t>();
+    a.cell_rptr = h->cell_rptr.as<int64_t>();
+    a.cell_rows = h->cell_rows.as<int32_t>();
+    a.cell_cnt = h->cell_cnt.as<int32_t>();
+    a.val = h->vals[dtype].csr.as<VT>();
+    a.valT = h->vals[dtype].csc.as<VT>();
+    a.D = scaled ? h->colscale.as<double>() : nullptr;
+    a.lam_rows_on = lamrows ? 1 : 0;
+    if (w) {
+        a.ubar = w->ubar.as<ST>();
+        a.vbar = w->vbar.as<ST>();
+        a.vsc = scaled ? w->vsc.as<ST>() : w->vbar.as<ST>();
+        a.x = w->x.as<double>();
+        a.wv = w->wv.as<double>();
+        a.partial = w->partial.as<double>();
+        a.sc = w->scal.as<LsqrScalars>();
+        a.sy = w->sync.as<LsqrSync>();
+    }
+    return a;
+}
+
+template <class K> static unsigned persistent_grid(K kernel, int device, int64_t work_items) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LT, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)num_sms(device) * per_sm;
+    int64_t need = (work_items + LT - 1) / LT;
+    if (need < 1) need = 1;
+    if (g > need) g = need;
+    if (g > MAXBLK) g = MAXBLK;
+    return (unsigned)g;
+}
+
+template <class VT, class ST, int FMT> struct Solver {
+    static pdst_status prepare(pdst_handle *h, LsqrWork *w, bool lamrows) {
+        const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
+        PDST_TRY(w->ubar.alloc(sizeof(ST) * std::max<int64_t>(M, 1)));
+        PDST_TRY(w->vbar.alloc(sizeof(ST) * std::max<int32_t>(h->n, 1)));
+        PDST_TRY(w->vsc.alloc(sizeof(ST) * std::max<int32_t>(h->n, 1)));
+        PDST_TRY(w->x.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+        PDST_TRY(w->wv.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+        PDST_TRY(w->partial.alloc(sizeof(double) * 3 * MAXBLK));
+        PDST_TRY(w->scal.alloc(sizeof(LsqrScalars)));
+        PDST_TRY(w->sync.alloc(sizeof(LsqrSync)));
+        if (!w->h_scal) PDST_CUDA(cudaMallocHost(&w->h_scal, sizeof(LsqrScalars)));
+        w->M = M;
+        // warp-per-row kernels: items = rows * 32 threads
+        w->grid_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
+        w->grid_cols = persistent_grid(k_adj<VT, ST, FMT>, h->device, (int64_t)h->n * 32);
+        w->grid_vec = persistent_grid(k_upd<ST>, h->device, h->n);
+        return PDST_OK;
+    }
+
+    static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
+        k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
+        k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+    }
+
+    static pdst_status run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
+                           const double *d, const LsqrScalars &init, int kblock, bool use_graph,
+                           double *m_out, cudaStream_t s) {
+        OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, scaled, lamrows);
+        PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
+        *w->h_scal = init;
+        PDST_CUDA(cudaMemcpyAsync(w->scal.p, w->h_scal, sizeof(LsqrScalars),
+                                  cudaMemcpyHostToDevice, s));
+        unsigned ginit = persistent_grid(k_init<ST>, h->device, w->M);
+        k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, a.ubar, a.x, a.wv, a.partial, a.sc,
+                                        a.sy);
+        k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+        PDST_CUDA(cudaGetLastError());
+
+        cudaGraphExec_t exec = nullptr;
+        if (use_graph) {
+            auto it = w->graphs.find(kblock);
+            if (it != w->graphs.end()) {
+                exec = it->second;
+            } else {
+                cudaStream_t cs;
+                PDST_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, cs);
+                    e = cudaStreamEndCapture(cs, &g);
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                if (e != cudaSuccess) {
+                    set_error("LSQR graph capture: %s", cudaGetErrorString(e));
+                    return PDST_ERR_CUDA;
+                }
+                w->graphs[kblock] = exec;
+            }
+        }
+        for (;;) {
+            PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
+                                      cudaMemcpyDeviceToHost, s));
+            PDST_CUDA(cudaStreamSynchronize(s));
+            const LsqrScalars &c = *w->h_scal;
+            if (c.done || c.istop || c.itn >= c.itmax) break;
+            if (exec) {
+                PDST_CUDA(cudaGraphLaunch(exec, s));
+            } else {
+                for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, s);
+                PDST_CUDA(cudaGetLastError());
+            }
+        }
+        k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out);
+        PDST_CUDA(cudaGetLastError());
+        PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
+                                  cudaMemcpyDeviceToHost, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        return PDST_OK;
+    }
+};
+
+template <class VT, class ST, int FMT>
+static pdst_status dispatch_run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
+                                const double *d, const LsqrScalars &init, int kblock,
+                                bool use_graph, double *m_out, cudaStream_t s, bool fresh) {
+    if (fresh) PDST_TRY((Solver<VT, ST, FMT>::prepare(h, w, lamrows)));
+    return Solver<VT, ST, FMT>::run(h, w, dtype, scaled, lamrows, d, init, kblock, use_graph,
+                                    m_out, s);
+}
+
+static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, double lam,
+                             int32_t itmax, double tol, double *m_out, pdst_lsqr_info *info,
+                             const pdst_lsqr_opts *o, cudaStream_t s) {
+    pdst_lsqr_opts opts;
+    pdst_lsqr_opts_default(&opts);
+    if (o) opts = *o;
+    const int dtype = opts.dtype, fmt = opts.format;
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_lsqr: unknown dtype %d", dtype);
+    PDST_CHECK_ARG(fmt == PDST_FMT_ELEMENT || fmt == PDST_FMT_BLOCKED, "pdst_lsqr: unknown format");
+    PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr: itmax must be >= 0");
+    PDST_CHECK_ARG(std::isfinite(w_s) && w_s >= 0.0, "pdst_lsqr: w must be finite and >= 0");
+    PDST_CHECK_ARG(std::isfinite(lam) && lam >= 0.0, "pdst_lsqr: lambda must be finite and >= 0");
+    PDST_CHECK_ARG(std::isfinite(tol) && tol >= 0.0, "pdst_lsqr: tol must be finite and >= 0");
+    PDST_CHECK_ARG(h->m == 0 || d_dev, "pdst_lsqr: d is NULL");
+    PDST_CHECK_ARG(m_out, "pdst_lsqr: m_out is NULL");
+    if (!h->vals[dtype].present) {
+        set_error("pdst_lsqr: values of dtype %d were not kept by pdst_build_G", dtype);
+        return PDST_ERR_STATE;
+    }
+    if (fmt == PDST_FMT_ELEMENT && !(h->formats & (1u << PDST_FMT_ELEMENT))) {
+        set_error("pdst_lsqr: element indices were not built");
+        return PDST_ERR_STATE;
+    }
+    const bool scaled = opts.precond == 1;
+    if (scaled && !h->has_colscale) {
+        set_error("pdst_lsqr: precond = 1 needs pdst_set_col_scaling first");
+        return PDST_ERR_STATE;
+    }
+    PDST_CHECK_ARG(opts.precond == 0 || opts.precond == 1, "pdst_lsqr: unknown precond %d",
+                   opts.precond);
+    const bool lamrows = scaled && lam > 0.0;
+    const int kblock = opts.kblock > 0 ? opts.kblock : 16;
+    PDST_CHECK_ARG(kblock <= 1024, "pdst_lsqr: kblock must be <= 1024");
+
+    LsqrScalars init{};
+    init.cs2 = -1.0;
+    init.damp = scaled ? 0.0 : lam;
+    init.lam_rows = lamrows ? lam : 0.0;
+    init.atol = opts.atol >= 0.0 ? opts.atol : tol;
+    init.btol = opts.btol >= 0.0 ? opts.btol : tol;
+    const double conlim = opts.conlim > 0.0 ? opts.conlim : 1e8;
+    init.ctol = 1.0 / conlim;
+    init.w_smooth = w_s;
+    init.itmax = itmax;
+    init.hist = opts.rnorm_hist_dev;
+
+    if (!h->work) h->work = new LsqrWork();
+    LsqrWork *w = h->work;
+    const bool fresh = w->dtype != dtype || w->format != fmt || w->lamrows != (int)lamrows;
+    // captured graphs hold the workspace and scaling pointers: rebuild on change
+    const void *dptr = scaled ? h->colscale.p : nullptr;
+    if (fresh || w->graph_D != dptr) {
+        for (auto &g : w->graphs)
+            if (g.second) cudaGraphExecDestroy(g.second);
+        w->graphs.clear();
+        w->graph_D = dptr;
+    }
+    pdst_status st;
+    const bool ug = opts.use_graph != 0;
+    if (dtype == PDST_F64) {
+        st = fmt == PDST_FMT_ELEMENT
+                 ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
+                                                         kblock, ug, m_out, s, fresh)
+                 : dispatch_run<double, double, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
+                                                        kblock, ug, m_out, s, fresh);
+    } else if (dtype == PDST_F32) {
+        st = fmt == PDST_FMT_ELEMENT
+                 ? dispatch_run<float, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
+                                                       kblock, ug, m_out, s, fresh)
+                 : dispatch_run<float, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
+                                                      kblock, ug, m_out, s, fresh);
+    } else {
+        st = fmt == PDST_FMT_ELEMENT
+                 ? dispatch_run<__nv_bfloat16, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
+                                                               init, kblock, ug, m_out, s, fresh)
+                 : dispatch_run<__nv_bfloat16, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev,
+                                                              init, kblock, ug, m_out, s, fresh);
+    }
+    if (st != PDST_OK) {
+        w->dtype = -1;
+        return st;
+    }
+    w->dtype = dtype;
+    w->format = fmt;
+    w->lamrows = (int)lamrows;
+    const LsqrScalars &c = *w->h_scal;
+    if (info) {
+        info->iters = c.itn;
+        info->istop = c.istop;
+        info->rnorm = c.rnorm;
+        info->arnorm = c.arnorm;
+        info->anorm = c.anorm;
+        info->acond = c.acond;
+        info->xnorm = c.xnorm;
+        info->bnorm = c.bnorm;
+    }
+    if (c.err) {
+        set_error("pdst_lsqr: non-finite value in the LSQR recurrence (iteration %d)", c.itn);
+        return PDST_ERR_BREAKDOWN;
+    }
+    return PDST_OK;
+}
+
+pdst_status spmv_f64(pdst_handle *h, int dtype, int trans, const double *x, double *y,
+                     cudaStream_t s) {
+    const bool elem = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
+    const int64_t rows = trans ? h->n : h->m;
+    if (rows == 0) return PDST_OK;
+    if (dtype == PDST_F64) {
+        auto a = make_args<double, double>(h, dtype, nullptr, false, false);
+        if (elem) {
+            unsigned g = persistent_grid(k_spmv<double, FMT_ELEM>, h->device, rows * 32);
+            k_spmv<double, FMT_ELEM><<<g, LT, 0, s>>>(a, trans, x, y);
+        } else {
+            unsigned g = persistent_grid(k_spmv<double, FMT_BLK>, h->device, rows * 32);
+            k_spmv<double, FMT_BLK><<<g, LT, 0, s>>>(a, trans, x, y);
+        }
+    } else if (dtype == PDST_F32) {
+        auto a = make_args<float, double>(h, dtype, nullptr, false, false);
+        if (elem) {
+            unsigned g = persistent_grid(k_spmv<float, FMT_ELEM>, h->device, rows * 32);
+            k_spmv<float, FMT_ELEM><<<g, LT, 0, s>>>(a, trans, x, y);
+        } else {
+            unsigned g = persistent_grid(k_spmv<float, FMT_BLK>, h->device, rows * 32);
+            k_spmv<float, FMT_BLK><<<g, LT, 0, s>>>(a, trans, x, y);
+        }
+    } else {
+        auto a = make_args<__nv_bfloat16, double>(h, dtype, nullptr, false, false);
+        if (elem) {
+            unsigned g = persistent_grid(k_spmv<__nv_bfloat16, FMT_ELEM>, h->device, rows * 32);
+            k_spmv<__nv_bfloat16, FMT_ELEM><<<g, LT, 0, s>>>(a, trans, x, y);
+        } else {
+            unsigned g = persistent_grid(k_spmv<__nv_bfloat16, FMT_BLK>, h->device, rows * 32);
+            k_spmv<__nv_bfloat16, FMT_BLK><<<g, LT, 0, s>>>(a, trans, x, y);
+        }
+    }
+    PDST_CUDA(cudaGetLastError());
+    return PDST_OK;
+}
+
+static pdst_status colnorm_scaling(pdst_handle *h, double w, double lam, double *D,
+                                   cudaStream_t s) {
+    if (h->n == 0) return PDST_OK;
+    if (h->vals[PDST_F64].present) {
+        auto a = make_args<double, double>(h, PDST_F64, nullptr, false, false);
+        unsigned g = persistent_grid(k_colnorm_scale<double>, h->device, (int64_t)h->n * 32);
+        k_colnorm_scale<double><<<g, LT, 0, s>>>(a, w, lam, D);
+    } else if (h->vals[PDST_F32].present) {
+        auto a = make_args<float, double>(h, PDST_F32, nullptr, false, false);
+        unsigned g = persistent_grid(k_colnorm_scale<float>, h->device, (int64_t)h->n * 32);
+        k_colnorm_scale<float><<<g, LT, 0, s>>>(a, w, lam, D);
+    } else {
+        auto a = make_args<__nv_bfloat16, double>(h, PDST_BF16, nullptr, false, false);
+        unsigned g = persistent_grid(k_colnorm_scale<__nv_bfloat16>, h->device, (int64_t)h->n * 32);
+        k_colnorm_scale<__nv_bfloat16><<<g, LT, 0, s>>>(a, w, lam, D);
+    }
+    PDST_CUDA(cudaGetLastError());
+    return PDST_OK;
+}
+
+}  // namespace pdst
+
+using namespace pdst;
+
+extern "C" void pdst_lsqr_opts_default(pdst_lsqr_opts *o) {
+    if (!o) return;
+    o->dtype = PDST_F64;
+    o->format = PDST_FMT_ELEMENT;
+    o->atol = -1.0;
+    o->btol = -1.0;
+    o->conlim = 0.0;
+    o->precond = 0;
+    o->kblock = 16;
+    o->use_graph = 1;
+    o->reserved = 0;
+    o->rnorm_hist_dev = nullptr;
+}
+
+extern "C" pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lambda,
+                                 int32_t itmax, double tol, double *m_out_dev,
+                                 pdst_lsqr_info *info, const pdst_lsqr_opts *opts, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_lsqr: handle is NULL");
+    return lsqr_impl(h, d_dev, w, lambda, itmax, tol, m_out_dev, info, opts,
+                     (cudaStream_t)stream);
+}
+
+extern "C" pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w,
+                                      double lambda, int32_t itmax, double tol,
+                                      double *m_out_host, pdst_lsqr_info *info,
+                                      const pdst_lsqr_opts *opts, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_lsqr_host: handle is NULL");
+    PDST_CHECK_ARG(h->m == 0 || d_host, "pdst_lsqr_host: d is NULL");
+    PDST_CHECK_ARG(m_out_host, "pdst_lsqr_host: m_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    static thread_local DevBuf dd, mm;
+    PDST_TRY(dd.alloc(sizeof(double) * std::max<int64_t>(h->m, 1)));
+    PDST_TRY(mm.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+    if (h->m)
+        PDST_CUDA(cudaMemcpyAsync(dd.p, d_host, sizeof(double) * h->m, cudaMemcpyHostToDevice, s));
+    PDST_TRY(lsqr_impl(h, dd.as<double>(), w, lambda, itmax, tol, mm.as<double>(), info, opts, s));
+    PDST_CUDA(cudaMemcpyAsync(m_out_host, mm.p, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaStreamSynchronize(s));
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_apply_G(pdst_handle_t h, int32_t dtype, int32_t trans,
+                                    const double *x_dev, double *y_dev, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_apply_G: handle is NULL");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_apply_G: unknown dtype");
+    PDST_CHECK_ARG(trans == 0 || trans == 1, "pdst_apply_G: trans must be 0 or 1");
+    PDST_CHECK_ARG(x_dev && y_dev, "pdst_apply_G: NULL vector");
+    if (!h->vals[dtype].present) {
+        set_error("pdst_apply_G: values of dtype %d were not kept", dtype);
+        return PDST_ERR_STATE;
+    }
+    return spmv_f64(h, dtype, trans, x_dev, y_dev, (cudaStream_t)stream);
+}
+
+extern "C" pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev, double w,
+                                            double lambda, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_set_col_scaling: handle is NULL");
+    PDST_CHECK_ARG(std::isfinite(w) && std::isfinite(lambda) && w >= 0 && lambda >= 0,
+                   "pdst_set_col_scaling: w and lambda must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    PDST_TRY(h->colscale.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+    if (D_dev) {
+        PDST_CUDA(cudaMemcpyAsync(h->colscale.p, D_dev, sizeof(double) * h->n,
+                                  cudaMemcpyDeviceToDevice, s));
+    } else {
+        PDST_TRY(colnorm_scaling(h, w, lambda, h->colscale.as<double>(), s));
+    }
+    PDST_CUDA(cudaStreamSynchronize(s));
+    h->has_colscale = true;
+    return PDST_OK;
+}
