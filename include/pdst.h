@@ -139,7 +139,8 @@ typedef struct {
     int32_t precond;   /* 0 none; 1 right diagonal scaling set by pdst_set_col_scaling */
     int32_t kblock;    /* iterations per graph launch (<= 0: 16) */
     int32_t use_graph; /* 1 (default): CUDA graph replay; 0: plain launches */
-    int32_t reserved;
+    int32_t profile;   /* 1: one iteration per launch group, each kernel bracketed by CUDA
+                          events; per-kernel device time returned in pdst_lsqr_info */
     double *rnorm_hist_dev; /* optional device array (itmax): ||r|| after each iteration */
 } pdst_lsqr_opts;
 
@@ -157,6 +158,11 @@ typedef struct {
     double acond;    /* estimate of cond(A) */
     double xnorm;    /* estimate of ||x|| (of y when scaled) */
     double bnorm;    /* ||d|| */
+    int32_t kernel_launches; /* kernels this call launched (graph nodes included) */
+    int32_t profiled_iters;  /* iterations covered by the *_ms fields (profile = 1) */
+    double fwd_ms;   /* total device time of the forward kernel A v (profile = 1) */
+    double adj_ms;   /* total device time of the adjoint kernel A^T u + recurrence */
+    double upd_ms;   /* total device time of the x/w update kernel */
 } pdst_lsqr_info;
 
 /*

@@ -611,6 +611,11 @@ template <class K> static unsigned persistent_grid(K kernel, int device, int64_t
     return (unsigned)g;
 }
 
+struct RunStats {
+    int launches = 0, profiled_iters = 0;
+    double fwd_ms = 0, adj_ms = 0, upd_ms = 0;
+};
+
 template <class VT, class ST, int FMT> struct Solver {
     static pdst_status prepare(pdst_handle *h, LsqrWork *w, bool lamrows) {
         const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
@@ -637,9 +642,40 @@ template <class VT, class ST, int FMT> struct Solver {
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
     }
 
+    // Per-kernel device time of `iters` plain-launched iterations, each kernel
+    // bracketed by CUDA events on the launching stream.
+    static pdst_status profiled_block(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a,
+                                      int iters, cudaStream_t s, RunStats &rs) {
+        std::vector<cudaEvent_t> ev(4 * (size_t)iters);
+        for (auto &e : ev) PDST_CUDA(cudaEventCreate(&e));
+        for (int i = 0; i < iters; ++i) {
+            cudaEventRecord(ev[4 * i], s);
+            k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
+            cudaEventRecord(ev[4 * i + 1], s);
+            k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+            cudaEventRecord(ev[4 * i + 2], s);
+            k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+            cudaEventRecord(ev[4 * i + 3], s);
+        }
+        PDST_CUDA(cudaGetLastError());
+        PDST_CUDA(cudaStreamSynchronize(s));
+        rs.launches += 3 * iters;
+        for (int i = 0; i < iters; ++i) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            cudaEventElapsedTime(&t0, ev[4 * i], ev[4 * i + 1]);
+            cudaEventElapsedTime(&t1, ev[4 * i + 1], ev[4 * i + 2]);
+            cudaEventElapsedTime(&t2, ev[4 * i + 2], ev[4 * i + 3]);
+            rs.fwd_ms += t0;
+            rs.adj_ms += t1;
+            rs.upd_ms += t2;
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        return PDST_OK;
+    }
+
     static pdst_status run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                            const double *d, const LsqrScalars &init, int kblock, bool use_graph,
-                           double *m_out, cudaStream_t s) {
+                           bool profile, double *m_out, cudaStream_t s, RunStats &rs) {
         OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, scaled, lamrows);
         PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
         *w->h_scal = init;
@@ -651,9 +687,10 @@ template <class VT, class ST, int FMT> struct Solver {
         k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
         PDST_CUDA(cudaGetLastError());
+        rs.launches += 3;
 
         cudaGraphExec_t exec = nullptr;
-        if (use_graph) {
+        if (use_graph && !profile) {
             auto it = w->graphs.find(kblock);
             if (it != w->graphs.end()) {
                 exec = it->second;
@@ -682,18 +719,24 @@ template <class VT, class ST, int FMT> struct Solver {
             PDST_CUDA(cudaStreamSynchronize(s));
             const LsqrScalars &c = *w->h_scal;
             if (c.done || c.istop || c.itn >= c.itmax) break;
-            if (exec) {
+            if (profile) {
+                PDST_TRY(profiled_block(h, w, a, 1, s, rs));
+            } else if (exec) {
                 PDST_CUDA(cudaGraphLaunch(exec, s));
+                rs.launches += 3 * kblock;
             } else {
                 for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, s);
                 PDST_CUDA(cudaGetLastError());
+                rs.launches += 3 * kblock;
             }
         }
         k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out);
         PDST_CUDA(cudaGetLastError());
+        rs.launches += 1;
         PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
                                   cudaMemcpyDeviceToHost, s));
         PDST_CUDA(cudaStreamSynchronize(s));
+        if (profile) rs.profiled_iters = w->h_scal->itn;
         return PDST_OK;
     }
 };
@@ -701,10 +744,11 @@ template <class VT, class ST, int FMT> struct Solver {
 template <class VT, class ST, int FMT>
 static pdst_status dispatch_run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                                 const double *d, const LsqrScalars &init, int kblock,
-                                bool use_graph, double *m_out, cudaStream_t s, bool fresh) {
+                                bool use_graph, bool profile, double *m_out, cudaStream_t s,
+                                bool fresh, RunStats &rs) {
     if (fresh) PDST_TRY((Solver<VT, ST, FMT>::prepare(h, w, lamrows)));
     return Solver<VT, ST, FMT>::run(h, w, dtype, scaled, lamrows, d, init, kblock, use_graph,
-                                    m_out, s);
+                                    profile, m_out, s, rs);
 }
 
 static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, double lam,
@@ -766,24 +810,26 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     }
     pdst_status st;
     const bool ug = opts.use_graph != 0;
+    const bool prof = opts.profile != 0;
+    RunStats rs;
     if (dtype == PDST_F64) {
         st = fmt == PDST_FMT_ELEMENT
                  ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                         kblock, ug, m_out, s, fresh)
+                                                         kblock, ug, prof, m_out, s, fresh, rs)
                  : dispatch_run<double, double, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                        kblock, ug, m_out, s, fresh);
+                                                        kblock, ug, prof, m_out, s, fresh, rs);
     } else if (dtype == PDST_F32) {
         st = fmt == PDST_FMT_ELEMENT
                  ? dispatch_run<float, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                       kblock, ug, m_out, s, fresh)
+                                                       kblock, ug, prof, m_out, s, fresh, rs)
                  : dispatch_run<float, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                      kblock, ug, m_out, s, fresh);
+                                                      kblock, ug, prof, m_out, s, fresh, rs);
     } else {
         st = fmt == PDST_FMT_ELEMENT
                  ? dispatch_run<__nv_bfloat16, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
-                                                               init, kblock, ug, m_out, s, fresh)
+                                                               init, kblock, ug, prof, m_out, s, fresh, rs)
                  : dispatch_run<__nv_bfloat16, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev,
-                                                              init, kblock, ug, m_out, s, fresh);
+                                                              init, kblock, ug, prof, m_out, s, fresh, rs);
     }
     if (st != PDST_OK) {
         w->dtype = -1;
@@ -802,6 +848,11 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         info->acond = c.acond;
         info->xnorm = c.xnorm;
         info->bnorm = c.bnorm;
+        info->kernel_launches = rs.launches;
+        info->profiled_iters = prof ? rs.profiled_iters : 0;
+        info->fwd_ms = rs.fwd_ms;
+        info->adj_ms = rs.adj_ms;
+        info->upd_ms = rs.upd_ms;
     }
     if (c.err) {
         set_error("pdst_lsqr: non-finite value in the LSQR recurrence (iteration %d)", c.itn);
@@ -881,7 +932,7 @@ extern "C" void pdst_lsqr_opts_default(pdst_lsqr_opts *o) {
     o->precond = 0;
     o->kblock = 16;
     o->use_graph = 1;
-    o->reserved = 0;
+    o->profile = 0;
     o->rnorm_hist_dev = nullptr;
 }
 
