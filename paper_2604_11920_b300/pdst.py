@@ -1,0 +1,258 @@
+"""Python binding of the C ABI in include/pdst.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libpdst.so built in-tree by
+``paper_2604_11920_b300.build``; this module only converts arguments.  There
+is no fallback: if the library is missing or fails to load, calls raise.
+PyTorch is used for device memory and streams (``torch.Tensor.data_ptr()``,
+``torch.cuda.current_stream()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpdst.so")
+
+F64, F32, BF16 = 0, 1, 2
+FMT_ELEMENT, FMT_BLOCKED = 0, 1
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+FORMATS = {"element": FMT_ELEMENT, "blocked": FMT_BLOCKED}
+
+STATUS = {0: "PDST_OK", 1: "PDST_ERR_ARG", 2: "PDST_ERR_CUDA", 3: "PDST_ERR_OOM",
+          4: "PDST_ERR_BREAKDOWN", 5: "PDST_ERR_TIMEOUT", 6: "PDST_ERR_NOT_CONVERGED",
+          7: "PDST_ERR_LIMIT", 8: "PDST_ERR_STATE"}
+
+
+class PdstError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx_km", ctypes.c_double), ("dz_km", ctypes.c_double)]
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("value_dtypes", ctypes.c_uint32), ("formats", ctypes.c_uint32)]
+
+
+class LsqrOpts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("format", ctypes.c_int32),
+                ("atol", ctypes.c_double), ("btol", ctypes.c_double),
+                ("conlim", ctypes.c_double), ("precond", ctypes.c_int32),
+                ("kblock", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p)]
+
+
+class LsqrInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("istop", ctypes.c_int32),
+                ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
+                ("anorm", ctypes.c_double), ("acond", ctypes.c_double),
+                ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int32), ("profiled_iters", ctypes.c_int32),
+                ("fwd_ms", ctypes.c_double), ("adj_ms", ctypes.c_double),
+                ("upd_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32, _i64, _d = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+# name -> (restype, argtypes); must match include/pdst.h
+SIGNATURES = {
+    "pdst_build_G": (_i32, [ctypes.POINTER(Grid), _i64, _vp, _vp, _i32, _vp,
+                            ctypes.POINTER(BuildOpts), _vp, ctypes.POINTER(_vp)]),
+    "pdst_destroy": (_i32, [_vp]),
+    "pdst_G_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                           ctypes.POINTER(_i64)]),
+    "pdst_G_export_csr": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pdst_G_export_csc": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pdst_apply_G": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    "pdst_lsqr_opts_default": (None, [ctypes.POINTER(LsqrOpts)]),
+    "pdst_lsqr": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
+                         ctypes.POINTER(LsqrOpts), _vp]),
+    "pdst_lsqr_host": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
+                              ctypes.POINTER(LsqrOpts), _vp]),
+    "pdst_set_col_scaling": (_i32, [_vp, _vp, _d, _d, _vp]),
+    "pdst_last_error_string": (ctypes.c_char_p, []),
+    "pdst_version": (_i32, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libpdst.so (raises if it is missing; run build() first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2604_11920_b300.build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PdstError(status, load().pdst_last_error_string().decode())
+
+
+def _stream(stream=None):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, numel=None, dtype=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, precond=0,
+              kblock=16, use_graph=True, hist=None, profile=False) -> LsqrOpts:
+    o = LsqrOpts()
+    load().pdst_lsqr_opts_default(ctypes.byref(o))
+    o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    o.format = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    o.atol, o.btol, o.conlim = atol, btol, conlim
+    o.precond, o.kblock, o.use_graph = int(precond), int(kblock), int(bool(use_graph))
+    o.profile = int(bool(profile))
+    o.rnorm_hist_dev = None if hist is None else hist.data_ptr()
+    return o
+
+
+@dataclass
+class Result:
+    m: object
+    info: dict
+
+
+class Handle:
+    """Owns one device-resident G (CSR + transpose) built by pdst_build_G."""
+
+    def __init__(self, ptr: ctypes.c_void_p, grid: Grid):
+        self._ptr = ptr
+        self.grid = grid
+        m, n, nnz = _i64(), _i32(), _i64()
+        _check(load().pdst_G_info(self._ptr, ctypes.byref(m), ctypes.byref(n),
+                                  ctypes.byref(nnz)))
+        self.m, self.n, self.nnz = m.value, n.value, nnz.value
+
+    def close(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.pdst_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        if self._ptr is None:
+            raise ValueError("handle is closed")
+        return self._ptr
+
+    # -- inspection -------------------------------------------------------
+    def export_csr(self, dtype="f64"):
+        ptr = np.zeros(self.m + 1, np.int64)
+        idx = np.zeros(self.nnz, np.int32)
+        val = np.zeros(self.nnz, np.float64)
+        _check(load().pdst_G_export_csr(self.ptr, DTYPES[dtype], _np_ptr(ptr), _np_ptr(idx),
+                                        _np_ptr(val)))
+        return ptr, idx, val
+
+    def export_csc(self, dtype="f64"):
+        ptr = np.zeros(self.n + 1, np.int64)
+        idx = np.zeros(self.nnz, np.int32)
+        val = np.zeros(self.nnz, np.float64)
+        _check(load().pdst_G_export_csc(self.ptr, DTYPES[dtype], _np_ptr(ptr), _np_ptr(idx),
+                                        _np_ptr(val)))
+        return ptr, idx, val
+
+    def apply_G(self, x, y, trans=False, dtype="f64", stream=None):
+        import torch
+        nin, nout = (self.m, self.n) if trans else (self.n, self.m)
+        _check(load().pdst_apply_G(self.ptr, DTYPES[dtype], int(trans),
+                                   _dev_ptr(x, nin, torch.float64, "x"),
+                                   _dev_ptr(y, nout, torch.float64, "y"), _stream(stream)))
+        return y
+
+    # -- solves ---------------------------------------------------------------
+    def lsqr(self, d, w, lam, itmax, tol, m_out=None, stream=None, **opt_kw) -> Result:
+        import torch
+        if m_out is None:
+            m_out = torch.empty(self.n, dtype=torch.float64, device=d.device)
+        info = LsqrInfo()
+        o = lsqr_opts(**opt_kw)
+        _check(load().pdst_lsqr(self.ptr, _dev_ptr(d, self.m, torch.float64, "d"), w, lam,
+                                int(itmax), tol, _dev_ptr(m_out, self.n, torch.float64, "m_out"),
+                                ctypes.byref(info), ctypes.byref(o), _stream(stream)))
+        return Result(m_out, info.as_dict())
+
+    def lsqr_host(self, d: np.ndarray, w, lam, itmax, tol, m_out: Optional[np.ndarray] = None,
+                  stream=None, **opt_kw) -> Result:
+        if d.dtype != np.float64 or not d.flags["C_CONTIGUOUS"] or d.shape != (self.m,):
+            raise ValueError("d must be a contiguous float64 vector of length m")
+        if m_out is None:
+            m_out = np.zeros(self.n, np.float64)
+        info = LsqrInfo()
+        o = lsqr_opts(**opt_kw)
+        _check(load().pdst_lsqr_host(self.ptr, _np_ptr(d), w, lam, int(itmax), tol,
+                                     _np_ptr(m_out), ctypes.byref(info), ctypes.byref(o),
+                                     _stream(stream)))
+        return Result(m_out, info.as_dict())
+
+    def set_col_scaling(self, D=None, w=0.0, lam=0.0, stream=None):
+        import torch
+        p = ctypes.c_void_p(None) if D is None else _dev_ptr(D, self.n, torch.float64, "D")
+        _check(load().pdst_set_col_scaling(self.ptr, p, w, lam, _stream(stream)))
+
+
+def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=("f64", "f32"),
+            formats=("element", "blocked"), stream=None) -> Handle:
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 6)
+    row_period = np.ascontiguousarray(row_period, dtype=np.int32)
+    kdz = np.ascontiguousarray(kdz, dtype=np.float64)
+    grid = Grid(nx, ny, nz, dx_km, dz_km)
+    opts = BuildOpts(sum(1 << DTYPES[d] for d in dtypes), sum(1 << FORMATS[f] for f in formats))
+    out = ctypes.c_void_p()
+    _check(load().pdst_build_G(ctypes.byref(grid), ctrl.shape[0], _np_ptr(ctrl),
+                               _np_ptr(row_period), int(n_periods), _np_ptr(kdz),
+                               ctypes.byref(opts), _stream(stream), ctypes.byref(out)))
+    return Handle(out, grid)
+
+
+def build_G_problem(p, **kw) -> Handle:
+    """pdst_build_G for a generator problem (see synth.py)."""
+    return build_G(p.nx, p.ny, p.nz, p.dx_km, p.dz_km, p.ctrl, p.row_period, p.n_periods,
+                   p.kdz, **kw)
