@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: LSQR time-to-tolerance of the regularised traveltime solve.
+
+Workload (default): the 64 x 64 x 16 system (65,536 unknowns; 120 stations,
+7,140 pairs x 24 periods = 171,360 rows; Bezier rays; Gaussian-blob model,
+2 % noise; w = 2, lambda = 0.05; tol 1e-6), synthetic inputs from the seeded
+generator.  One step = one LSQR solve to tolerance on the device-resident G
+(forward product, adjoint product, FP64 recurrence and x/w update, all in the
+library's kernels, replayed from a CUDA graph).  The G assembly is timed
+separately (`build_G_s`).
+
+Reported beside the headline: the plain FP64 GPU LSQR on the same system (FP64
+values and vectors, element CSR/CSC, no scaling, graph on), the model error of
+both against an FP64 reference solve, a per-kernel roofline from CUDA events,
+the end-to-end time through the host entry point, and the FP64 CPU oracle
+timed on this machine's cores on a bounded sample.
+
+`--impl reference` times the FP64 CPU oracle alone (the comparison arm).
+Multi-GPU (torchrun): every rank solves its own system (seed + rank); no data
+moves between ranks ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LSQR time-to-tol (s) & SpMV/SpMV^T HBM GB/s vs plain FP64 GPU LSQR, 1xB300"
+
+FORMS = {
+    # name: (dtype, format, precond)
+    "f64-element": ("f64", "element", 0),
+    "f64-blocked": ("f64", "blocked", 0),
+    "f32-element": ("f32", "element", 0),
+    "f32-blocked": ("f32", "blocked", 0),
+    "f32-blocked-colnorm": ("f32", "blocked", 1),
+    "bf16-blocked-colnorm": ("bf16", "blocked", 1),
+}
+PLAIN = "f64-element"
+DEFAULT_FORM = "f32-blocked-colnorm"
+VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pdst", "reference"], default="pdst")
+    ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
+    ap.add_argument("--form", choices=sorted(FORMS), default=DEFAULT_FORM)
+    ap.add_argument("--cpu-sample-iters", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time the chosen form only (for profiler runs)")
+    return ap.parse_args()
+
+
+def make_problem(name, rank):
+    from paper_2604_11920_b300 import synth
+    return {"mid": synth.mid, "tiny": synth.tiny, "large": synth.large}[name](
+        seed={"mid": 1, "tiny": 0, "large": 2}[name] + 1000 * rank)
+
+
+def workload_desc(p):
+    return (f"{p.nx}x{p.ny}x{p.nz} grid ({p.n} unknowns), {p.stations.shape[0]} stations, "
+            f"{p.pairs.shape[0]} pairs x {p.n_periods} periods = {p.m_rows} rows, "
+            f"w={p.w}, lambda={p.lam}, tol={p.tol}")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+        self.enabled = enabled
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p > 0.3 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power)}
+
+
+# ------------------------------------------------------------- roofline
+
+def algorithmic_bytes(h, p, dtype, fmt, scaled):
+    """Bytes each kernel must move once per launch: matrix arrays read once,
+    vectors read/written once, gathered vectors counted once (L2-resident)."""
+    vb, xb = VALUE_BYTES[dtype], VEC_BYTES[dtype]
+    m, n, nnz, nz = h.m, h.n, h.nnz, p.nz
+    U, H = nnz // nz, p.nx * p.ny
+    M = m + n + (n if scaled else 0)
+    if fmt == "element":
+        fwd_idx = 4 * nnz + 8 * (m + 1)
+        adj_idx = 4 * nnz + 8 * (n + 1)
+    else:
+        fwd_idx = 4 * U + 8 * (m + 1)
+        adj_idx = 4 * U + 8 * (H + 1) + 4 * H
+    fwd = vb * nnz + fwd_idx + 2 * xb * M + xb * n
+    adj = vb * nnz + adj_idx + xb * M + 2 * xb * n + (xb * n + 8 * n if scaled else 0)
+    upd = xb * n + 8 * n * 3
+    return {"fwd": fwd, "adj": adj, "upd": upd}
+
+
+def dram_traffic_record(kernel, form, workload):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"```json\n(.*?)\n```", open(path).read(), re.S)
+    if not m:
+        return None
+    try:
+        rec = json.loads(m.group(1))
+    except json.JSONDecodeError:
+        return None
+    src = os.path.join(ROOT, "paper_2604_11920_b300", "csrc", "lsqr.cu")
+    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for r in rec.get("records", []):
+        if (r.get("kernel") == kernel and r.get("form") == form and r.get("workload") == workload
+                and r.get("lsqr_cu_sha1") == digest):
+            return r.get("bytes_per_launch")
+    return None
+
+
+# ------------------------------------------------------------------ arms
+
+def run_pdst(args, rank, world):
+    import torch
+
+    from paper_2604_11920_b300 import pdst
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    pdst.load()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    p = make_problem(args.workload, rank)
+    dtype, fmt, precond = FORMS[args.form]
+    dtypes = sorted({"f64", dtype})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = pdst.build_G_problem(p, dtypes=tuple(dtypes))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+
+    # right-hand side d = G m_true + 2 % noise (input synthesis on the device)
+    mt = torch.from_numpy(p.m_true).cuda()
+    gm = torch.empty(h.m, dtype=torch.float64, device="cuda")
+    h.apply_G(mt, gm, dtype="f64")
+    rms = torch.sqrt(torch.mean(gm * gm))
+    d = gm + p.noise_frac * rms * torch.from_numpy(p.noise).cuda()
+    itmax = p.itmax
+    if precond:
+        h.set_col_scaling(None, p.w, p.lam)
+
+    def solve(form, tol=p.tol, **kw):
+        dt, fm, pc = FORMS[form]
+        return h.lsqr(d, p.w, p.lam, itmax, tol, dtype=dt, fmt=fm, precond=pc, **kw)
+
+    def timed(form, steps, warmup):
+        for _ in range(warmup):
+            solve(form)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        e0.record(stream)
+        for _ in range(steps):
+            r = solve(form)
+            launches += r.info["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, r, launches
+
+    with ClockSampler(dev, enabled=not args.no_clocks) as clk:
+        ms, res, launches = timed(args.form, args.steps, args.warmup)
+    clocks = clk.summary()
+    if args.only_solve:
+        if rank == 0:
+            print(json.dumps({"form": args.form, "ms_per_solve": ms, "iters": res.info["iters"],
+                              "istop": res.info["istop"]}))
+        return
+
+    out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": dtype, "data": "synthetic (seeded generator; no dataset)"}
+    m_chosen = res.m.clone()
+    it_chosen = res.info["iters"]
+
+    # plain FP64 GPU LSQR on the same system
+    if args.form != PLAIN:
+        ms_plain, res_plain, _ = timed(PLAIN, max(1, min(args.steps, 3)), 1)
+    else:
+        ms_plain, res_plain = ms, res
+    m_plain = res_plain.m.clone()
+    # FP64 reference solution at a tighter tolerance
+    ref = solve(PLAIN, tol=p.tol * 1e-3)
+
+    def relerr(a):
+        return float(torch.linalg.norm(a - ref.m) / torch.linalg.norm(ref.m))
+
+    # per-kernel device time (events around each launch, same solve)
+    prof = solve(args.form, profile=True)
+    pi = max(prof.info["profiled_iters"], 1)
+    kms = {"fwd": prof.info["fwd_ms"] / pi, "adj": prof.info["adj_ms"] / pi,
+           "upd": prof.info["upd_ms"] / pi}
+    ab = algorithmic_bytes(h, p, dtype, fmt, bool(precond))
+    dom = max(("fwd", "adj"), key=lambda k: kms[k])
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = ab[dom] / (kms[dom] * 1e-3) / 1e9
+    kernel_name = {"fwd": "k_fwd", "adj": "k_adj"}[dom]
+    out["roofline"] = {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1),
+                       "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                       "traffic": dram_traffic_record(kernel_name, args.form, args.workload),
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
+                       if "hbm_gbs" in peaks else "fallback 6400 GB/s",
+                       "algorithmic_bytes_per_launch": ab[dom],
+                       "avg_launch_ms": round(kms[dom], 5)}
+    spmv_gbs = {k: round(ab[k] / (kms[k] * 1e-3) / 1e9, 1) for k in ("fwd", "adj")}
+
+    # end to end through the host entry point (pinned host d and m)
+    e2e = None
+    if not args.no_e2e:
+        dh = torch.empty(h.m, dtype=torch.float64, pin_memory=True)
+        dh.copy_(d.cpu())
+        mh = torch.empty(h.n, dtype=torch.float64, pin_memory=True)
+        dn, mn = dh.numpy(), mh.numpy()
+        dt_, fm_, pc_ = FORMS[args.form]
+        h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=pc_)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=pc_)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * h.m,
+               "d2h_bytes_per_step": 8 * h.n}
+
+    out.update({
+        "config": {"workload": workload_desc(p), "form": args.form,
+                   "plain_form": PLAIN, "nnz": h.nnz,
+                   "l2_policy": "inputs larger than L2 (G values+indices "
+                                f"{(VALUE_BYTES[dtype] * 2 * h.nnz) / 1e9:.2f} GB > 126 MB)",
+                   "step": "one LSQR solve to tol on device-resident G (graph replay)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "iters": it_chosen,
+        "istop": res.info["istop"],
+        "model_error_vs_fp64_ref": relerr(m_chosen),
+        "plain_fp64": {"s": ms_plain / 1e3, "iters": res_plain.info["iters"],
+                       "model_error_vs_fp64_ref": relerr(m_plain)},
+        "speedup_vs_plain_fp64": ms_plain / ms,
+        "kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
+        "spmv_gbs": spmv_gbs,
+        "build_G_s": build_s,
+        "iters_per_s": it_chosen / (ms / 1e3),
+    })
+
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, args.cpu_sample_iters, res_plain.info["iters"])
+    h.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(p, sample_iters, iters_to_tol):
+    """FP64 CPU oracle on this machine's cores: a bounded sample of LSQR
+    iterations on the same system, scaled to the FP64 iteration count."""
+    import oracle
+    oracle.build()
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    t0 = time.perf_counter()
+    r = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0,
+                    itmax=sample_iters)
+    t = time.perf_counter() - t0
+    per_it = t / max(r.itn, 1)
+    return {"value": per_it * iters_to_tol, "unit": "s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{r.itn} FP64 oracle LSQR iterations on the same system in {t:.2f} s, "
+                      f"scaled to the {iters_to_tol} iterations the FP64 solve needs to reach tol",
+            "s_per_iter": per_it}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = make_problem(args.workload, 0)
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    grid = (p.nx, p.ny, p.nz)
+    # iteration count to tolerance of the oracle itself (untimed, once)
+    full = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=p.tol, btol=p.tol, itmax=p.itmax)
+    sample = args.cpu_sample_iters
+    for _ in range(args.warmup):
+        oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0, itmax=3)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0, itmax=sample)
+        times.append((time.perf_counter() - t0) / r.itn)
+    per_it = statistics.mean(times)
+    value = per_it * full.itn
+    cb = {"value": value, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"{sample} FP64 oracle LSQR iterations per step, scaled to the oracle's "
+                    f"own {full.itn} iterations to tol"}
+    print(json.dumps({"metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": per_it * sample * 1e3, "higher_is_better": False,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic (seeded generator; no dataset)",
+                      "config": {"workload": workload_desc(p), "form": "oracle-f64"},
+                      "impl": "reference", "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "pdst":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_pdst(args, rank, world)
+    finally:
+        if world > 1 and args.impl == "pdst":
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
