@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(LT) k_adj(OpArgs<VT, ST> a, int init) {
                 if (a.lam_rows_on) s += lamr * (AT)a.ubar[a.m + a.n + j];
                 AT dj = a.D ? (AT)a.D[j] : (AT)1;
                 s *= dj;
-                AT v = s * ib - cv * a.vbar[j];
+                // the start step does not read v-bar: the buffer may hold another
+                // dtype's bits from an earlier solve on this handle
+                AT v = init ? s * ib : s * ib - cv * a.vbar[j];
                 a.vbar[j] = v;
                 if (a.D) a.vsc[j] = dj * v;
                 ss += (double)v * (double)v;
