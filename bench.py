@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the chosen form only (for profiler runs)")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="small profiler case: build G in the chosen form only and run 3 "
+                         "LSQR iterations with plain launches (no timing)")
     return ap.parse_args()
 
 
@@ -188,6 +191,25 @@ def dram_traffic_record(kernel, form, workload):
 
 
 # ------------------------------------------------------------------ arms
+
+def run_ncu_case(args):
+    """Three LSQR iterations of the chosen form with plain launches: the case
+    profiled by ncu (one k_fwd and one k_adj launch per iteration)."""
+    import torch
+
+    from paper_2604_11920_b300 import pdst
+    torch.cuda.set_device(0)
+    p = make_problem(args.workload, 0)
+    dtype, fmt, precond = FORMS[args.form]
+    h = pdst.build_G_problem(p, dtypes=(dtype,), formats=(fmt,))
+    d = torch.from_numpy(p.noise).cuda()
+    if precond:
+        h.set_col_scaling(None, p.w, p.lam)
+    r = h.lsqr(d, p.w, p.lam, 3, 0.0, dtype=dtype, fmt=fmt, precond=precond, use_graph=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.form, "iters": r.info["iters"], "nnz": h.nnz}))
+    h.close()
+
 
 def run_pdst(args, rank, world):
     import torch
@@ -416,6 +438,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.ncu_case:
+            run_ncu_case(args)
         else:
             run_pdst(args, rank, world)
     finally:
