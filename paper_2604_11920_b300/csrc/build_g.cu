@@ -565,6 +565,19 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
         set_error("G assembly: per-row cell list inconsistent between passes (code %d)", herr);
         return PDST_ERR_CUDA;
     }
+    // work order of the transpose products: longest cells first, so that the
+    // last work items of a launch are the short ones
+    {
+        std::vector<int32_t> cnt(H), order(H);
+        PDST_CUDA(cudaMemcpy(cnt.data(), h->cell_cnt.p, sizeof(int32_t) * H,
+                             cudaMemcpyDeviceToHost));
+        for (int i = 0; i < H; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return cnt[a] > cnt[b]; });
+        PDST_TRY(h->cell_order.alloc(sizeof(int32_t) * H));
+        PDST_CUDA(cudaMemcpy(h->cell_order.p, order.data(), sizeof(int32_t) * H,
+                             cudaMemcpyHostToDevice));
+    }
     return PDST_OK;
 }
 

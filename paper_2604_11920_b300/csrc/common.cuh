@@ -136,6 +136,7 @@ struct pdst_handle {
     pdst::DevBuf cell_rptr;    // int64 [H+1]  run pointer per cell (transpose)
     pdst::DevBuf cell_rows;    // int32 [U]    rows of each cell (ascending)
     pdst::DevBuf cell_cnt;     // int32 [H]    rows per cell
+    pdst::DevBuf cell_order;   // int32 [H]    cells by descending row count (work order)
     // element indices (PDST_FMT_ELEMENT)
     pdst::DevBuf row_ptr;      // int64 [m+1]
     pdst::DevBuf col;          // int32 [nnz]

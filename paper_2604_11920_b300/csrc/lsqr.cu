@@ -43,6 +43,7 @@ template <class VT, class ST> struct OpArgs {
     const int64_t *cell_rptr;
     const int32_t *cell_rows;
     const int32_t *cell_cnt;
+    const int32_t *cell_order;
     const VT *val;            // CSR order
     const VT *valT;           // CSC order
     const double *D;          // right diagonal scaling or nullptr
@@ -211,6 +212,202 @@ __device__ __forceinline__ AT laplace(const XT *__restrict__ x, int64_t j, int n
     return s;
 }
 
+
+// ------------------------------------------- blocked products, LSQR sweeps
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Unroll depth of the streaming loops: enough independent 16-byte loads per
+// lane to cover HBM latency at 32 resident warps per SM.
+template <class AT> struct Unroll { static constexpr int U = 4; };
+template <> struct Unroll<double> { static constexpr int U = 2; };
+
+// Cell of run `ee` of the current row: runs 0..63 come from the two registers
+// c0, c1 holding the row's first 64 cells (read by shuffle), later runs from
+// memory.  Every lane of the warp must call it.
+__device__ __forceinline__ int run_cell(uint32_t ee, int c0, int c1,
+                                        const int32_t *__restrict__ cells, int64_t e0, bool ok) {
+    int a = __shfl_sync(FULL, c0, ee & 31u);
+    int b = __shfl_sync(FULL, c1, ee & 31u);
+    if (ee < 32u) return a;
+    if (ee < 64u) return b;
+    return ok ? __ldg(cells + e0 + ee) : 0;
+}
+
+// Lane partial of one blocked CSR row (nz % 4 == 0): every group of four
+// entries lies in one run and multiplies a contiguous 4-vector of x.  The
+// loop is warp-uniform; UN groups per lane are loaded before any is used.
+template <class VT, class AT, class XT>
+__device__ __forceinline__ AT blk_row_partial(const VT *__restrict__ vrow,
+                                              const XT *__restrict__ x,
+                                              const int32_t *__restrict__ cells, int64_t e0,
+                                              uint32_t nrun, uint32_t nz, int lane, int c0,
+                                              int c1) {
+    constexpr int UN = Unroll<AT>::U;
+    const uint32_t len = nrun * nz;
+    const uint32_t se = 128u / nz, sk = 128u % nz;
+    uint32_t ee = (4u * lane) / nz, kk = 4u * lane - ((4u * lane) / nz) * nz;
+    AT s = 0;
+    for (uint32_t base = 0; base < len; base += 128u * UN) {
+        typename Wide<VT>::T v[UN][4];
+        XT xv[UN][4];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const uint32_t rel = base + 4u * lane + 128u * u;
+            const bool ok = rel < len;
+            const int h = run_cell(ee, c0, c1, cells, e0, ok);
+            if (ok) {
+                Pack4<VT>::ld(vrow + rel, v[u]);
+                ldx4<XT>(x + (int64_t)h * nz + kk, xv[u]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    v[u][t] = 0;
+                    xv[u][t] = 0;
+                }
+            }
+            ee += se;
+            kk += sk;
+            if (kk >= nz) {
+                kk -= nz;
+                ++ee;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s += (AT)v[u][t] * (AT)xv[u][t];
+    }
+    return s;
+}
+
+// G rows of the forward sweep in the blocked layout: warp per row, the next
+// row's run pointers prefetched while the current row streams.
+template <class VT, class ST>
+__device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, ST cu,
+                                               int64_t gw, int64_t nw, int lane) {
+    using AT = ST;
+    double ss = 0.0;
+    const uint32_t nz = (uint32_t)a.nz;
+    int64_t r = gw, e0 = 0, e1 = 0;
+    if (r < a.m) {
+        e0 = __ldg(a.row_cptr + r);
+        e1 = __ldg(a.row_cptr + r + 1);
+    }
+    while (r < a.m) {
+        const int64_t rn = r + nw;
+        int64_t e0n = 0, e1n = 0;
+        if (rn < a.m) {
+            e0n = __ldg(a.row_cptr + rn);
+            e1n = __ldg(a.row_cptr + rn + 1);
+        }
+        const uint32_t nrun = (uint32_t)(e1 - e0);
+        AT part;
+        if ((nz & 3u) == 0u) {
+            const int c0 = (uint32_t)lane < nrun ? __ldg(a.row_cells + e0 + lane) : 0;
+            const int c1 = (uint32_t)lane + 32u < nrun ? __ldg(a.row_cells + e0 + 32 + lane) : 0;
+            part = blk_row_partial<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc, a.row_cells, e0,
+                                               nrun, nz, lane, c0, c1);
+        } else {
+            part = 0;
+            const uint32_t len = nrun * nz;
+            for (uint32_t rel = lane; rel < len; rel += 32u) {
+                const uint32_t ee = rel / nz, k = rel - ee * nz;
+                const int h = __ldg(a.row_cells + e0 + ee);
+                part += (AT)widen(a.val[e0 * (int64_t)nz + rel]) * (AT)__ldg(a.vsc + (int64_t)h * nz + k);
+            }
+        }
+        const AT dot = warp_sum(part);
+        if (lane == 0) {
+            AT u = dot * ia - cu * a.ubar[r];
+            a.ubar[r] = u;
+            ss += (double)u * (double)u;
+        }
+        r = rn;
+        e0 = e0n;
+        e1 = e1n;
+    }
+    return ss;
+}
+
+// Final value of column j of the adjoint sweep from its G^T u dot product:
+// add w L^T u2 (+ lambda u3), scale by D_j, subtract (beta/alpha) v-bar_j.
+template <class VT, class ST>
+__device__ __forceinline__ double adj_finish(const OpArgs<VT, ST> &a, int64_t j, ST dot, ST ib,
+                                             ST cv, ST wsm, ST lamr, int init) {
+    using AT = ST;
+    AT s = dot + wsm * laplace<AT, ST>(a.ubar + a.m, j, a.nx, a.ny, a.nz);
+    if (a.lam_rows_on) s += lamr * (AT)a.ubar[a.m + a.n + j];
+    const AT dj = a.D ? (AT)a.D[j] : (AT)1;
+    s *= dj;
+    // the start step does not read v-bar: the buffer may hold another dtype's
+    // bits from an earlier solve on this handle
+    const AT v = init ? s * ib : s * ib - cv * a.vbar[j];
+    a.vbar[j] = v;
+    if (a.D) a.vsc[j] = dj * v;
+    return (double)v * (double)v;
+}
+
+// G^T rows of the adjoint sweep in the blocked layout.  Work item = (cell,
+// group of up to four depths), cells in descending length order: the warp
+// reads each row index of the cell once, gathers u once per row and streams
+// the four depth columns' values (contiguous in the CSC value order).
+template <class VT, class ST>
+__device__ __forceinline__ double adj_cols_blk(const OpArgs<VT, ST> &a, ST ib, ST cv, ST wsm,
+                                               ST lamr, int init, int64_t gw, int64_t nw,
+                                               int lane) {
+    using AT = ST;
+    constexpr int UN = Unroll<AT>::U;
+    const int nz = a.nz;
+    const int kg = (nz + 3) >> 2;
+    const int64_t H = (int64_t)a.nx * a.ny;
+    const int64_t items = H * kg;
+    double ss = 0.0;
+    for (int64_t it = gw; it < items; it += nw) {
+        const int h = __ldg(a.cell_order + it / kg);
+        const int k0 = 4 * (int)(it % kg);
+        const int nk = nz - k0 < 4 ? nz - k0 : 4;
+        const int64_t c0 = __ldg(a.cell_rptr + h);
+        const int cnt = __ldg(a.cell_cnt + h);
+        const VT *vb = a.valT + (int64_t)nz * c0 + (int64_t)k0 * cnt;
+        const int32_t *rows = a.cell_rows + c0;
+        AT acc[4] = {0, 0, 0, 0};
+        for (int qb = 0; qb < cnt; qb += 32 * UN) {
+            int rr[UN];
+            AT uu[UN];
+            AT vv[UN][4];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int q = qb + lane + 32 * u;
+                rr[u] = q < cnt ? __ldg(rows + q) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int q = qb + lane + 32 * u;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    vv[u][t] = (q < cnt && t < nk) ? (AT)ldval(vb + (int64_t)t * cnt + q) : (AT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) uu[u] = rr[u] >= 0 ? (AT)__ldg(a.ubar + rr[u]) : (AT)0;
+#pragma unroll
+            for (int u = 0; u < UN; ++u)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[t] += vv[u][t] * uu[u];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[t] = warp_sum(acc[t]);
+        if (lane < nk) {
+            AT mine = acc[0];
+            if (lane == 1) mine = acc[1];
+            if (lane == 2) mine = acc[2];
+            if (lane == 3) mine = acc[3];
+            ss += adj_finish(a, (int64_t)h * nz + k0 + lane, mine, ib, cv, wsm, lamr, init);
+        }
+    }
+    return ss;
+}
+
 // ------------------------------------------------------------- reductions
 
 // Block sum of v, then the block that finishes last sums the per-block
@@ -366,14 +563,16 @@ __global__ void __launch_bounds__(LT) k_fwd(OpArgs<VT, ST> a) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
-    for (int64_t r = gw; r < a.m; r += nw) {
-        AT dot = FMT == FMT_ELEM
-                     ? dot_elem<VT, AT, ST>(a.row_ptr, a.col, a.val, a.vsc, r, lane)
-                     : dot_blk_row<VT, AT, ST>(a.row_cptr, a.row_cells, a.val, a.vsc, r, a.nz, lane);
-        if (lane == 0) {
-            AT u = dot * ia - cu * a.ubar[r];
-            a.ubar[r] = u;
-            ss += (double)u * (double)u;
+    if (FMT == FMT_BLK) {
+        ss = fwd_rows_blk<VT, ST>(a, ia, cu, gw, nw, lane);
+    } else {
+        for (int64_t r = gw; r < a.m; r += nw) {
+            AT dot = dot_elem<VT, AT, ST>(a.row_ptr, a.col, a.val, a.vsc, r, lane);
+            if (lane == 0) {
+                AT u = dot * ia - cu * a.ubar[r];
+                a.ubar[r] = u;
+                ss += (double)u * (double)u;
+            }
         }
     }
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,22 +618,12 @@ __global__ void __launch_bounds__(LT) k_adj(OpArgs<VT, ST> a, int init) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
     if (!skip) {
-        for (int64_t j = gw; j < a.n; j += nw) {
-            AT dot = FMT == FMT_ELEM
-                         ? dot_elem<VT, AT, ST>(a.col_ptr, a.row_idx, a.valT, a.ubar, j, lane)
-                         : dot_blk_col<VT, AT, ST>(a.cell_rptr, a.cell_cnt, a.cell_rows, a.valT,
-                                                   a.ubar, j, a.nz, lane);
-            if (lane == 0) {
-                AT s = dot + wsm * laplace<AT, ST>(a.ubar + a.m, j, a.nx, a.ny, a.nz);
-                if (a.lam_rows_on) s += lamr * (AT)a.ubar[a.m + a.n + j];
-                AT dj = a.D ? (AT)a.D[j] : (AT)1;
-                s *= dj;
-                // the start step does not read v-bar: the buffer may hold another
-                // dtype's bits from an earlier solve on this handle
-                AT v = init ? s * ib : s * ib - cv * a.vbar[j];
-                a.vbar[j] = v;
-                if (a.D) a.vsc[j] = dj * v;
-                ss += (double)v * (double)v;
+        if (FMT == FMT_BLK) {
+            ss = adj_cols_blk<VT, ST>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+        } else {
+            for (int64_t j = gw; j < a.n; j += nw) {
+                AT dot = dot_elem<VT, AT, ST>(a.col_ptr, a.row_idx, a.valT, a.ubar, j, lane);
+                if (lane == 0) ss += adj_finish(a, j, dot, ib, cv, wsm, lamr, init);
             }
         }
     }
@@ -584,6 +773,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     a.cell_rptr = h->cell_rptr.as<int64_t>();
     a.cell_rows = h->cell_rows.as<int32_t>();
     a.cell_cnt = h->cell_cnt.as<int32_t>();
+    a.cell_order = h->cell_order.as<int32_t>();
     a.val = h->vals[dtype].csr.as<VT>();
     a.valT = h->vals[dtype].csc.as<VT>();
     a.D = scaled ? h->colscale.as<double>() : nullptr;

@@ -76,13 +76,27 @@ def test_converged_fp64_matches_oracle(tiny, fmt):
 @pytest.mark.parametrize("dtype,fmt", [("f32", "element"), ("f32", "blocked"),
                                        ("bf16", "blocked")])
 def test_reduced_precision_forms(tiny, dtype, fmt):
+    """FP32 values/vectors (FP64 scalars) reach the FP64 form's accuracy at the
+    same stopping tolerance, and the model error of each form is reported;
+    BF16 values carry a ~4e-3 relative value error, so only a looser bound."""
     p, G, GT, d, h, ref = tiny
-    res = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype=dtype, fmt=fmt)
-    err = rel(res.m.cpu().numpy(), ref.x)
-    print(f"{dtype}/{fmt}: iters={res.info['iters']} istop={res.info['istop']} "
-          f"model error vs FP64 oracle {err:.3e}")
-    assert res.info["istop"] in (1, 2)
-    assert err <= (2e-3 if dtype == "f32" else 2e-2)
+    out = {}
+    for tol in (1e-6, 1e-8):
+        r64 = h.lsqr(to_dev(d), p.w, p.lam, 20000, tol, dtype="f64", fmt=fmt)
+        res = h.lsqr(to_dev(d), p.w, p.lam, 20000, tol, dtype=dtype, fmt=fmt)
+        e64 = rel(r64.m.cpu().numpy(), ref.x)
+        err = rel(res.m.cpu().numpy(), ref.x)
+        out[tol] = (err, e64)
+        print(f"{dtype}/{fmt} tol={tol:g}: iters={res.info['iters']} istop={res.info['istop']} "
+              f"model error vs FP64 oracle {err:.3e} (FP64 form: {e64:.3e}, "
+              f"{r64.info['iters']} iters)")
+        assert res.info["istop"] in (1, 2, 7)
+    err6, e646 = out[1e-6]
+    if dtype == "f32":
+        assert err6 <= 1.5 * e646 + 1e-4
+        assert out[1e-8][0] <= MODEL_TOL
+    else:
+        assert err6 <= 3.0 * e646 + 2e-2
 
 
 def test_switching_forms_on_one_handle(tiny):
