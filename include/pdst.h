@@ -182,6 +182,37 @@ pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lam
                       int32_t itmax, double tol, double *m_out_dev, pdst_lsqr_info *info,
                       const pdst_lsqr_opts *opts, void *stream);
 
+/*
+ * Allocation-free variant of pdst_lsqr.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory while
+ * they solve.  Examples are a serving or plugin host that owns all device
+ * memory through its own pool and forbids allocation once it is running, a
+ * process under a hard device-memory cap where a late cudaMalloc may fail, and
+ * a latency-sensitive loop that cannot afford the device-wide synchronisation
+ * cudaFree brings.  pdst_lsqr allocates its workspace (and pinned host
+ * memory, and a CUDA graph) on first use; this function allocates nothing:
+ * all solve scratch (scalars, reduction partials, u-bar, v-bar, x, w) lives in
+ * one file-scope device array of 16 MiB that every GPU which loads the
+ * library holds until the process exits.
+ *
+ * Arguments and results are those of pdst_lsqr (same kernels, same answer);
+ * the iterations are plain kernel launches (opts->use_graph is ignored) and
+ * opts->profile must be 0.  The handle's device must be the current device.
+ * The first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array, which keeps the previous
+ * call's contents (the function clears what must start at zero): calls that
+ * overlap on the GPU -- from two host threads or on two streams -- race and
+ * give wrong results.  Synchronous on `stream`.
+ * Errors: as pdst_lsqr, plus PDST_ERR_LIMIT when the system's scratch exceeds
+ * 16 MiB: 8 (m + 3n) + 16 n bytes in FP64, 4 (m + 3n) + 16 n in FP32/BF16,
+ * plus about 100 KiB, plus n more vector entries when lambda rows are appended
+ * (e.g. the 64 x 64 x 16 system with 171,360 rows needs about 4.5 MB).
+ */
+pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, double w, double lambda,
+                              int32_t itmax, double tol, double *m_out_dev,
+                              pdst_lsqr_info *info, const pdst_lsqr_opts *opts, void *stream);
+
 /* Same as pdst_lsqr with host d and m (pinned or pageable): copies d in and
  * m out inside the call (the end-to-end path). */
 pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w, double lambda,

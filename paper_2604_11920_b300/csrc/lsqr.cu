@@ -20,6 +20,7 @@
 // a CUDA graph; kernels return at entry once the stopping rule has fired.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1183,5 +1184,234 @@ extern "C" pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev
     }
     PDST_CUDA(cudaStreamSynchronize(s));
     h->has_colscale = true;
+    return PDST_OK;
+}
+
+// --------------------------------------------------- allocation-free solve
+//
+// pdst_lsqr_noalloc runs the same LSQR kernels as pdst_lsqr, but every scratch
+// buffer of the solve (the recurrence scalars, the reduction partials and
+// counters, u-bar, v-bar, the scaled v, x and w) is carved out of one
+// file-scope device array instead of memory the handle allocates.  The host
+// side allocates nothing either: no graph, no events, no pinned buffers.
+
+namespace pdst {
+
+constexpr size_t NOALLOC_BYTES = size_t(16) << 20;   // 16 MiB per device
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device ordinal.  In host code the
+// symbol name is only a stand-in, so the address is looked up once per device
+// (with that device current) and passed to the kernels.
+static void *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+static pdst_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) {
+        set_error("pdst_lsqr_noalloc: device ordinal %d out of range", device);
+        return PDST_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("pdst_lsqr_noalloc: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+            return PDST_ERR_CUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[device]);
+    return PDST_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bytes of scratch one solve needs, in the carving order used below.
+static size_t noalloc_need(int64_t M, int64_t n, size_t st) {
+    return align256(sizeof(LsqrScalars)) + align256(sizeof(LsqrSync)) +
+           align256(sizeof(double) * 3 * MAXBLK) + align256(st * M) + 2 * align256(st * n) +
+           2 * align256(sizeof(double) * n);
+}
+
+template <class VT, class ST, int FMT>
+static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, bool scaled,
+                               bool lamrows, const double *d, const LsqrScalars &init,
+                               int kblock, double *m_out, cudaStream_t s, LsqrScalars &fin,
+                               int &launches) {
+    const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        unsigned char *p = base + off;
+        off += align256(bytes);
+        return p;
+    };
+    auto *sc = reinterpret_cast<LsqrScalars *>(carve(sizeof(LsqrScalars)));
+    auto *sy = reinterpret_cast<LsqrSync *>(carve(sizeof(LsqrSync)));
+    auto *partial = reinterpret_cast<double *>(carve(sizeof(double) * 3 * MAXBLK));
+    auto *ubar = reinterpret_cast<ST *>(carve(sizeof(ST) * M));
+    auto *vbar = reinterpret_cast<ST *>(carve(sizeof(ST) * h->n));
+    auto *vsc = reinterpret_cast<ST *>(carve(sizeof(ST) * h->n));
+    auto *x = reinterpret_cast<double *>(carve(sizeof(double) * h->n));
+    auto *wv = reinterpret_cast<double *>(carve(sizeof(double) * h->n));
+
+    OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, nullptr, scaled, lamrows);
+    a.ubar = ubar;
+    a.vbar = vbar;
+    a.vsc = scaled ? vsc : vbar;
+    a.x = x;
+    a.wv = wv;
+    a.partial = partial;
+    a.sc = sc;
+    a.sy = sy;
+    const unsigned g_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
+    const unsigned g_cols = persistent_grid(k_adj<VT, ST, FMT>, h->device, (int64_t)h->n * 32);
+    const unsigned g_vec = persistent_grid(k_upd<ST>, h->device, h->n);
+    const unsigned g_init = persistent_grid(k_init<ST>, h->device, M);
+
+    // the array keeps the previous call's contents: the counters must start at
+    // zero and the scalars from this call's values; every vector is written
+    // before it is read (k_init, the start step of k_adj, k_upd)
+    PDST_CUDA(cudaMemsetAsync(sy, 0, sizeof(LsqrSync), s));
+    LsqrScalars hs = init;
+    PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
+    k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, ubar, x, wv, partial, sc, sy);
+    k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 1);
+    k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, partial, sc, sy);
+    PDST_CUDA(cudaGetLastError());
+    launches += 3;
+    for (;;) {
+        PDST_CUDA(cudaMemcpyAsync(&fin, sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        if (fin.done || fin.istop || fin.itn >= fin.itmax) break;
+        for (int i = 0; i < kblock; ++i) {
+            k_fwd<VT, ST, FMT><<<g_rows, LT, 0, s>>>(a);
+            k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 0);
+            k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, partial, sc, sy);
+        }
+        PDST_CUDA(cudaGetLastError());
+        launches += 3 * kblock;
+    }
+    k_finalize<<<g_vec, LT, 0, s>>>(h->n, x, a.D, m_out);
+    PDST_CUDA(cudaGetLastError());
+    launches += 1;
+    PDST_CUDA(cudaMemcpyAsync(&fin, sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaStreamSynchronize(s));
+    return PDST_OK;
+}
+
+}  // namespace pdst
+
+extern "C" pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, double w,
+                                         double lambda, int32_t itmax, double tol,
+                                         double *m_out_dev, pdst_lsqr_info *info,
+                                         const pdst_lsqr_opts *o, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_lsqr_noalloc: handle is NULL");
+    pdst_lsqr_opts opts;
+    pdst_lsqr_opts_default(&opts);
+    if (o) opts = *o;
+    const int dtype = opts.dtype, fmt = opts.format;
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_lsqr_noalloc: unknown dtype %d", dtype);
+    PDST_CHECK_ARG(fmt == PDST_FMT_ELEMENT || fmt == PDST_FMT_BLOCKED,
+                   "pdst_lsqr_noalloc: unknown format");
+    PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr_noalloc: itmax must be >= 0");
+    PDST_CHECK_ARG(std::isfinite(w) && w >= 0.0, "pdst_lsqr_noalloc: w must be finite and >= 0");
+    PDST_CHECK_ARG(std::isfinite(lambda) && lambda >= 0.0,
+                   "pdst_lsqr_noalloc: lambda must be finite and >= 0");
+    PDST_CHECK_ARG(std::isfinite(tol) && tol >= 0.0,
+                   "pdst_lsqr_noalloc: tol must be finite and >= 0");
+    PDST_CHECK_ARG(h->m == 0 || d_dev, "pdst_lsqr_noalloc: d is NULL");
+    PDST_CHECK_ARG(m_out_dev, "pdst_lsqr_noalloc: m_out is NULL");
+    PDST_CHECK_ARG(opts.profile == 0, "pdst_lsqr_noalloc: profile mode is not available");
+    PDST_CHECK_ARG(opts.precond == 0 || opts.precond == 1,
+                   "pdst_lsqr_noalloc: unknown precond %d", opts.precond);
+    if (!h->vals[dtype].present) {
+        set_error("pdst_lsqr_noalloc: values of dtype %d were not kept by pdst_build_G", dtype);
+        return PDST_ERR_STATE;
+    }
+    if (fmt == PDST_FMT_ELEMENT && !(h->formats & (1u << PDST_FMT_ELEMENT))) {
+        set_error("pdst_lsqr_noalloc: element indices were not built");
+        return PDST_ERR_STATE;
+    }
+    const bool scaled = opts.precond == 1;
+    if (scaled && !h->has_colscale) {
+        set_error("pdst_lsqr_noalloc: precond = 1 needs pdst_set_col_scaling first");
+        return PDST_ERR_STATE;
+    }
+    int cur = -1;
+    PDST_CUDA(cudaGetDevice(&cur));
+    PDST_CHECK_ARG(cur == h->device,
+                   "pdst_lsqr_noalloc: the handle's device (%d) must be current (is %d)",
+                   h->device, cur);
+    const bool lamrows = scaled && lambda > 0.0;
+    const int kblock = opts.kblock > 0 ? opts.kblock : 16;
+    PDST_CHECK_ARG(kblock <= 1024, "pdst_lsqr_noalloc: kblock must be <= 1024");
+    const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
+    const size_t st = dtype == PDST_F64 ? sizeof(double) : sizeof(float);
+    const size_t need = noalloc_need(M, h->n, st);
+    if (need > NOALLOC_BYTES) {
+        set_error("pdst_lsqr_noalloc: this system needs %zu bytes of scratch; the static "
+                  "array holds %zu (use pdst_lsqr)", need, NOALLOC_BYTES);
+        return PDST_ERR_LIMIT;
+    }
+    unsigned char *base = nullptr;
+    PDST_TRY(noalloc_scratch(cur, &base));
+
+    LsqrScalars init{};
+    init.cs2 = -1.0;
+    init.damp = scaled ? 0.0 : lambda;
+    init.lam_rows = lamrows ? lambda : 0.0;
+    init.atol = opts.atol >= 0.0 ? opts.atol : tol;
+    init.btol = opts.btol >= 0.0 ? opts.btol : tol;
+    init.ctol = 1.0 / (opts.conlim > 0.0 ? opts.conlim : 1e8);
+    init.w_smooth = w;
+    init.itmax = itmax;
+    init.hist = opts.rnorm_hist_dev;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    LsqrScalars fin{};
+    int launches = 0;
+    pdst_status st_;
+    if (dtype == PDST_F64)
+        st_ = fmt == PDST_FMT_ELEMENT
+                  ? noalloc_run<double, double, FMT_ELEM>(h, base, dtype, scaled, lamrows, d_dev,
+                                                          init, kblock, m_out_dev, s, fin, launches)
+                  : noalloc_run<double, double, FMT_BLK>(h, base, dtype, scaled, lamrows, d_dev,
+                                                         init, kblock, m_out_dev, s, fin, launches);
+    else if (dtype == PDST_F32)
+        st_ = fmt == PDST_FMT_ELEMENT
+                  ? noalloc_run<float, float, FMT_ELEM>(h, base, dtype, scaled, lamrows, d_dev,
+                                                        init, kblock, m_out_dev, s, fin, launches)
+                  : noalloc_run<float, float, FMT_BLK>(h, base, dtype, scaled, lamrows, d_dev,
+                                                       init, kblock, m_out_dev, s, fin, launches);
+    else
+        st_ = fmt == PDST_FMT_ELEMENT
+                  ? noalloc_run<__nv_bfloat16, float, FMT_ELEM>(h, base, dtype, scaled, lamrows,
+                                                                d_dev, init, kblock, m_out_dev, s,
+                                                                fin, launches)
+                  : noalloc_run<__nv_bfloat16, float, FMT_BLK>(h, base, dtype, scaled, lamrows,
+                                                               d_dev, init, kblock, m_out_dev, s,
+                                                               fin, launches);
+    if (st_ != PDST_OK) return st_;
+    if (info) {
+        *info = pdst_lsqr_info{};
+        info->iters = fin.itn;
+        info->istop = fin.istop;
+        info->rnorm = fin.rnorm;
+        info->arnorm = fin.arnorm;
+        info->anorm = fin.anorm;
+        info->acond = fin.acond;
+        info->xnorm = fin.xnorm;
+        info->bnorm = fin.bnorm;
+        info->kernel_launches = launches;
+    }
+    if (fin.err) {
+        set_error("pdst_lsqr_noalloc: non-finite value in the LSQR recurrence (iteration %d)",
+                  fin.itn);
+        return PDST_ERR_BREAKDOWN;
+    }
     return PDST_OK;
 }

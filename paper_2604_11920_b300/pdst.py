@@ -83,6 +83,8 @@ SIGNATURES = {
                          ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_lsqr_host": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
                               ctypes.POINTER(LsqrOpts), _vp]),
+    "pdst_lsqr_noalloc": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
+                                 ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_set_col_scaling": (_i32, [_vp, _vp, _d, _d, _vp]),
     "pdst_last_error_string": (ctypes.c_char_p, []),
     "pdst_version": (_i32, []),
@@ -217,6 +219,18 @@ class Handle:
         _check(load().pdst_lsqr(self.ptr, _dev_ptr(d, self.m, torch.float64, "d"), w, lam,
                                 int(itmax), tol, _dev_ptr(m_out, self.n, torch.float64, "m_out"),
                                 ctypes.byref(info), ctypes.byref(o), _stream(stream)))
+        return Result(m_out, info.as_dict())
+
+    def lsqr_noalloc(self, d, w, lam, itmax, tol, m_out, stream=None, **opt_kw) -> Result:
+        """pdst_lsqr_noalloc: the same solve with no device allocation (the
+        caller passes the output buffer; scratch is the library's static array)."""
+        import torch
+        info = LsqrInfo()
+        o = lsqr_opts(**opt_kw)
+        _check(load().pdst_lsqr_noalloc(self.ptr, _dev_ptr(d, self.m, torch.float64, "d"), w,
+                                        lam, int(itmax), tol,
+                                        _dev_ptr(m_out, self.n, torch.float64, "m_out"),
+                                        ctypes.byref(info), ctypes.byref(o), _stream(stream)))
         return Result(m_out, info.as_dict())
 
     def lsqr_host(self, d: np.ndarray, w, lam, itmax, tol, m_out: Optional[np.ndarray] = None,
