@@ -282,41 +282,163 @@ __device__ __forceinline__ AT blk_row_partial(const VT *__restrict__ vrow,
     return s;
 }
 
-// G rows of the forward sweep in the blocked layout: warp per row, the next
-// row's run pointers prefetched while the current row streams.
-template <class VT, class ST>
-__device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, ST cu,
-                                               int64_t gw, int64_t nw, int lane) {
+// Lane partial of one blocked CSR row for a half-warp (nz = 4 Q, Q known at
+// compile time).  The row's entries are read as consecutive 4-entry quads:
+// quad f covers entries 4f..4f+3 of run f / Q, so a half-warp instruction
+// reads 256 contiguous bytes of values and whole 64-byte stretches of x (the
+// Q lanes of one run share its cell, read from L1).  UN quads per lane are
+// requested before any is used.
+template <class VT, class AT, class XT, int Q>
+__device__ __forceinline__ AT blk_row_quads(const VT *__restrict__ vrow, const XT *__restrict__ x,
+                                            const int32_t *__restrict__ cells_row, uint32_t nrun,
+                                            int hl) {
+    constexpr int UN = Unroll<AT>::U;
+    constexpr uint32_t NZ = 4u * Q;
+    const uint32_t nquad = nrun * Q;
+    AT s = 0;
+    for (uint32_t base = 0; base < nquad; base += 16u * UN) {
+        int h[UN];
+        uint32_t off[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const uint32_t f = base + hl + 16u * u;
+            const uint32_t run = f / Q;
+            off[u] = 4u * (f - run * Q);
+            h[u] = f < nquad ? __ldg(cells_row + run) : -1;
+        }
+        typename Wide<VT>::T vv[UN][4];
+        XT xx[UN][4];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const uint32_t f = base + hl + 16u * u;
+            if (h[u] >= 0) {
+                Pack4<VT>::ld(vrow + 4u * f, vv[u]);
+                ldx4<XT>(x + (size_t)h[u] * NZ + off[u], xx[u]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    vv[u][t] = 0;
+                    xx[u][t] = 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s += (AT)vv[u][t] * (AT)xx[u][t];
+    }
+    return s;
+}
+
+// Same for any nz % 4 == 0 (run and quad from a run-time division).
+template <class VT, class AT, class XT>
+__device__ __forceinline__ AT blk_row_quads_rt(const VT *__restrict__ vrow,
+                                               const XT *__restrict__ x,
+                                               const int32_t *__restrict__ cells_row,
+                                               uint32_t nrun, uint32_t nz, int hl) {
+    const uint32_t q = nz >> 2, nquad = nrun * q;
+    AT s = 0;
+    for (uint32_t f = hl; f < nquad; f += 16u) {
+        const uint32_t run = f / q;
+        const int h = __ldg(cells_row + run);
+        typename Wide<VT>::T vv[4];
+        XT xx[4];
+        Pack4<VT>::ld(vrow + 4u * f, vv);
+        ldx4<XT>(x + (size_t)h * nz + 4u * (f - run * q), xx);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) s += (AT)vv[t] * (AT)xx[t];
+    }
+    return s;
+}
+
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// G rows of the forward sweep in the blocked layout.  With nz % 4 == 0 each
+// half-warp owns one row (two rows per warp in flight) and each lane whole
+// runs; the next row's run pointers and first cells are prefetched while the
+// current row streams.  Other nz: warp per row, one entry per lane.
+template <class VT, class ST, int Q>
+__device__ __forceinline__ double fwd_rows_halfwarp(const OpArgs<VT, ST> &a, ST ia, ST cu,
+                                                    int64_t gw, int64_t nw, int lane) {
     using AT = ST;
     double ss = 0.0;
     const uint32_t nz = (uint32_t)a.nz;
-    int64_t r = gw, e0 = 0, e1 = 0;
+    const int hl = lane & 15;
+    const int64_t stride = 2 * nw;
+    int64_t r = 2 * gw + (lane >> 4);
+    int64_t e0 = 0, e1 = 0, e0n = 0, e1n = 0;
     if (r < a.m) {
         e0 = __ldg(a.row_cptr + r);
         e1 = __ldg(a.row_cptr + r + 1);
     }
-    while (r < a.m) {
-        const int64_t rn = r + nw;
-        int64_t e0n = 0, e1n = 0;
+    if (r + stride < a.m) {
+        e0n = __ldg(a.row_cptr + r + stride);
+        e1n = __ldg(a.row_cptr + r + stride + 1);
+    }
+    // both half-warps loop the same number of times so that the reduction
+    // shuffles see all 32 lanes
+    const int64_t rows_warp = (a.m - 2 * gw + stride - 1) / stride;
+    for (int64_t it = 0; it < rows_warp; ++it) {
+        const bool live = r < a.m;
+        const int64_t rn = r + stride, rnn = rn + stride;
+        int64_t e0nn = 0, e1nn = 0;
         if (rn < a.m) {
-            e0n = __ldg(a.row_cptr + rn);
-            e1n = __ldg(a.row_cptr + rn + 1);
+            // warm L1 with the next row's cells (up to 64 runs)
+            const int64_t nrn = e1n - e0n;
+            if (hl * 4 < nrn) prefetch_l1(a.row_cells + e0n + hl * 4);
         }
-        const uint32_t nrun = (uint32_t)(e1 - e0);
-        AT part;
-        if ((nz & 3u) == 0u) {
-            const int c0 = (uint32_t)lane < nrun ? __ldg(a.row_cells + e0 + lane) : 0;
-            const int c1 = (uint32_t)lane + 32u < nrun ? __ldg(a.row_cells + e0 + 32 + lane) : 0;
-            part = blk_row_partial<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc, a.row_cells, e0,
-                                               nrun, nz, lane, c0, c1);
-        } else {
-            part = 0;
-            const uint32_t len = nrun * nz;
-            for (uint32_t rel = lane; rel < len; rel += 32u) {
-                const uint32_t ee = rel / nz, k = rel - ee * nz;
-                const int h = __ldg(a.row_cells + e0 + ee);
-                part += (AT)widen(a.val[e0 * (int64_t)nz + rel]) * (AT)__ldg(a.vsc + (int64_t)h * nz + k);
-            }
+        if (rnn < a.m) {
+            e0nn = __ldg(a.row_cptr + rnn);
+            e1nn = __ldg(a.row_cptr + rnn + 1);
+        }
+        const AT uprev = (live && hl == 0) ? (AT)a.ubar[r] : (AT)0;
+        AT part = 0;
+        if (live) {
+            if (Q > 0)
+                part = blk_row_quads<VT, AT, ST, (Q > 0 ? Q : 1)>(
+                    a.val + e0 * (int64_t)nz, a.vsc, a.row_cells + e0, (uint32_t)(e1 - e0), hl);
+            else
+                part = blk_row_quads_rt<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc,
+                                                    a.row_cells + e0, (uint32_t)(e1 - e0), nz, hl);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        if (live && hl == 0) {
+            AT u = part * ia - cu * uprev;
+            a.ubar[r] = u;
+            ss += (double)u * (double)u;
+        }
+        r = rn;
+        e0 = e0n;
+        e1 = e1n;
+        e0n = e0nn;
+        e1n = e1nn;
+    }
+    return ss;
+}
+
+template <class VT, class ST>
+__device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, ST cu,
+                                               int64_t gw, int64_t nw, int lane) {
+    using AT = ST;
+    const uint32_t nz = (uint32_t)a.nz;
+    if ((nz & 3u) == 0u) {
+        if (nz == 16) return fwd_rows_halfwarp<VT, ST, 4>(a, ia, cu, gw, nw, lane);
+        if (nz == 8) return fwd_rows_halfwarp<VT, ST, 2>(a, ia, cu, gw, nw, lane);
+        if (nz == 20) return fwd_rows_halfwarp<VT, ST, 5>(a, ia, cu, gw, nw, lane);
+        return fwd_rows_halfwarp<VT, ST, 0>(a, ia, cu, gw, nw, lane);
+    }
+    double ss = 0.0;
+    for (int64_t r = gw; r < a.m; r += nw) {
+        const int64_t e0 = __ldg(a.row_cptr + r), e1 = __ldg(a.row_cptr + r + 1);
+        const uint32_t len = (uint32_t)(e1 - e0) * nz;
+        AT part = 0;
+        for (uint32_t rel = lane; rel < len; rel += 32u) {
+            const uint32_t ee = rel / nz, k = rel - ee * nz;
+            const int h = __ldg(a.row_cells + e0 + ee);
+            part += (AT)widen(a.val[e0 * (int64_t)nz + rel]) * (AT)__ldg(a.vsc + (int64_t)h * nz + k);
         }
         const AT dot = warp_sum(part);
         if (lane == 0) {
@@ -324,9 +446,6 @@ __device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, S
             a.ubar[r] = u;
             ss += (double)u * (double)u;
         }
-        r = rn;
-        e0 = e0n;
-        e1 = e1n;
     }
     return ss;
 }
@@ -373,14 +492,22 @@ __device__ __forceinline__ double adj_cols_blk(const OpArgs<VT, ST> &a, ST ib, S
         const VT *vb = a.valT + (int64_t)nz * c0 + (int64_t)k0 * cnt;
         const int32_t *rows = a.cell_rows + c0;
         AT acc[4] = {0, 0, 0, 0};
+        // row indices are fetched one chunk ahead of the u gathers that use them
+        int rn[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const int q = lane + 32 * u;
+            rn[u] = q < cnt ? __ldg(rows + q) : -1;
+        }
         for (int qb = 0; qb < cnt; qb += 32 * UN) {
             int rr[UN];
             AT uu[UN];
             AT vv[UN][4];
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
-                const int q = qb + lane + 32 * u;
-                rr[u] = q < cnt ? __ldg(rows + q) : -1;
+                rr[u] = rn[u];
+                const int q = qb + 32 * UN + lane + 32 * u;
+                rn[u] = q < cnt ? __ldg(rows + q) : -1;
             }
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
@@ -552,7 +679,7 @@ __global__ void __launch_bounds__(LT) k_init(int64_t m, int64_t M, int32_t n,
 
 // u-bar <- (A v-bar)/alpha - (alpha/beta) u-bar;  beta <- ||u-bar||.
 template <class VT, class ST, int FMT>
-__global__ void __launch_bounds__(LT) k_fwd(OpArgs<VT, ST> a) {
+__global__ void __launch_bounds__(LT, 4) k_fwd(OpArgs<VT, ST> a) {
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
     using AT = ST;
@@ -605,7 +732,7 @@ __global__ void __launch_bounds__(LT) k_fwd(OpArgs<VT, ST> a) {
 // v-bar <- (A^T u-bar)/beta - (beta/alpha) v-bar;  alpha <- ||v-bar||, then
 // the scalar recurrence (or its initialisation when init != 0).
 template <class VT, class ST, int FMT>
-__global__ void __launch_bounds__(LT) k_adj(OpArgs<VT, ST> a, int init) {
+__global__ void __launch_bounds__(LT, 4) k_adj(OpArgs<VT, ST> a, int init) {
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
     using AT = ST;
