@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "lsqr_dev.cuh"
 
 namespace pdst {
 
@@ -57,51 +58,6 @@ template <class VT, class ST> struct OpArgs {
     LsqrScalars *sc;
     LsqrSync *sy;
 };
-
-// ------------------------------------------------------------ load helpers
-
-template <class VT> struct Pack4;
-template <> struct Pack4<float> {
-    static __device__ __forceinline__ void ld(const float *p, float v[4]) {
-        float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-};
-template <> struct Pack4<double> {
-    static __device__ __forceinline__ void ld(const double *p, double v[4]) {
-        double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
-        double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-};
-template <> struct Pack4<__nv_bfloat16> {
-    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float v[4]) {
-        uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
-        v[0] = __uint_as_float(t.x << 16);
-        v[1] = __uint_as_float(t.x & 0xffff0000u);
-        v[2] = __uint_as_float(t.y << 16);
-        v[3] = __uint_as_float(t.y & 0xffff0000u);
-    }
-};
-template <class VT> struct Wide { using T = VT; };
-template <> struct Wide<__nv_bfloat16> { using T = float; };
-
-template <class ST> __device__ __forceinline__ void ldx4(const ST *p, ST v[4]);
-template <> __device__ __forceinline__ void ldx4<float>(const float *p, float v[4]) {
-    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-template <> __device__ __forceinline__ void ldx4<double>(const double *p, double v[4]) {
-    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
-__device__ __forceinline__ float ldval(const float *p) { return __ldcs(p); }
-__device__ __forceinline__ double ldval(const double *p) { return __ldcs(p); }
-__device__ __forceinline__ float ldval(const __nv_bfloat16 *p) {
-    return __bfloat162float(*p);
-}
 
 // ------------------------------------------------------------ dot products
 
@@ -195,92 +151,7 @@ __device__ __forceinline__ AT dot_blk_col(const int64_t *__restrict__ cell_rptr,
     return warp_sum(s0 + s1);
 }
 
-// (L x)_j = sum over existing 7-point neighbours i of (x_j - x_i).
-template <class AT, class XT>
-__device__ __forceinline__ AT laplace(const XT *__restrict__ x, int64_t j, int nx, int ny, int nz) {
-    const int k = (int)(j % nz);
-    const int64_t hh = j / nz;
-    const int ix = (int)(hh % nx), iy = (int)(hh / nx);
-    const int64_t sy = (int64_t)nx * nz;
-    const AT c = (AT)x[j];
-    AT s = 0;
-    if (k > 0) s += c - (AT)x[j - 1];
-    if (k < nz - 1) s += c - (AT)x[j + 1];
-    if (ix > 0) s += c - (AT)x[j - nz];
-    if (ix < nx - 1) s += c - (AT)x[j + nz];
-    if (iy > 0) s += c - (AT)x[j - sy];
-    if (iy < ny - 1) s += c - (AT)x[j + sy];
-    return s;
-}
-
-
 // ------------------------------------------- blocked products, LSQR sweeps
-
-constexpr unsigned FULL = 0xffffffffu;
-
-// Unroll depth of the streaming loops: enough independent 16-byte loads per
-// lane to cover HBM latency at 32 resident warps per SM.
-template <class AT> struct Unroll { static constexpr int U = 4; };
-template <> struct Unroll<double> { static constexpr int U = 2; };
-
-// Cell of run `ee` of the current row: runs 0..63 come from the two registers
-// c0, c1 holding the row's first 64 cells (read by shuffle), later runs from
-// memory.  Every lane of the warp must call it.
-__device__ __forceinline__ int run_cell(uint32_t ee, int c0, int c1,
-                                        const int32_t *__restrict__ cells, int64_t e0, bool ok) {
-    int a = __shfl_sync(FULL, c0, ee & 31u);
-    int b = __shfl_sync(FULL, c1, ee & 31u);
-    if (ee < 32u) return a;
-    if (ee < 64u) return b;
-    return ok ? __ldg(cells + e0 + ee) : 0;
-}
-
-// Lane partial of one blocked CSR row (nz % 4 == 0): every group of four
-// entries lies in one run and multiplies a contiguous 4-vector of x.  The
-// loop is warp-uniform; UN groups per lane are loaded before any is used.
-template <class VT, class AT, class XT>
-__device__ __forceinline__ AT blk_row_partial(const VT *__restrict__ vrow,
-                                              const XT *__restrict__ x,
-                                              const int32_t *__restrict__ cells, int64_t e0,
-                                              uint32_t nrun, uint32_t nz, int lane, int c0,
-                                              int c1) {
-    constexpr int UN = Unroll<AT>::U;
-    const uint32_t len = nrun * nz;
-    const uint32_t se = 128u / nz, sk = 128u % nz;
-    uint32_t ee = (4u * lane) / nz, kk = 4u * lane - ((4u * lane) / nz) * nz;
-    AT s = 0;
-    for (uint32_t base = 0; base < len; base += 128u * UN) {
-        typename Wide<VT>::T v[UN][4];
-        XT xv[UN][4];
-#pragma unroll
-        for (int u = 0; u < UN; ++u) {
-            const uint32_t rel = base + 4u * lane + 128u * u;
-            const bool ok = rel < len;
-            const int h = run_cell(ee, c0, c1, cells, e0, ok);
-            if (ok) {
-                Pack4<VT>::ld(vrow + rel, v[u]);
-                ldx4<XT>(x + (int64_t)h * nz + kk, xv[u]);
-            } else {
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    v[u][t] = 0;
-                    xv[u][t] = 0;
-                }
-            }
-            ee += se;
-            kk += sk;
-            if (kk >= nz) {
-                kk -= nz;
-                ++ee;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < UN; ++u)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) s += (AT)v[u][t] * (AT)xv[u][t];
-    }
-    return s;
-}
 
 // Lane partial of one blocked CSR row for a half-warp (nz = 4 Q, Q known at
 // compile time).  The row's entries are read as consecutive 4-entry quads:
@@ -351,14 +222,6 @@ __device__ __forceinline__ AT blk_row_quads_rt(const VT *__restrict__ vrow,
     return s;
 }
 
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-// G rows of the forward sweep in the blocked layout.  With nz % 4 == 0 each
-// half-warp owns one row (two rows per warp in flight) and each lane whole
-// runs; the next row's run pointers and first cells are prefetched while the
-// current row streams.  Other nz: warp per row, one entry per lane.
 template <class VT, class ST, int Q>
 __device__ __forceinline__ double fwd_rows_halfwarp(const OpArgs<VT, ST> &a, ST ia, ST cu,
                                                     int64_t gw, int64_t nw, int lane) {
@@ -568,81 +431,6 @@ __device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigne
     if (threadIdx.x == 0) *counter = 0u;
     total = s;
     return true;
-}
-
-// One LSQR step of the scalar recurrence (Paige & Saunders 1982): damping
-// rotation, plane rotation, x/w update coefficients, norm estimates and
-// stopping rules.  alpha_new = ||v-bar_{i+1}||, sc->beta = beta_{i+1},
-// sc->alpha = alpha_i, sc->wnorm2 = ||w_i||^2.
-__device__ void lsqr_step(LsqrScalars *sc, double alpha_new) {
-    const double alpha = sc->alpha, beta = sc->beta, damp = sc->damp;
-    const double dampsq = damp * damp;
-    if (beta > 0.0)
-        sc->anorm = sqrt(sc->anorm * sc->anorm + alpha * alpha + beta * beta + dampsq);
-    else
-        alpha_new = alpha;
-    double rhobar = sc->rhobar, phibar = sc->phibar, rhobar1 = rhobar, psi = 0.0;
-    if (damp > 0.0) {
-        rhobar1 = sqrt(rhobar * rhobar + dampsq);
-        const double cs1 = rhobar / rhobar1, sn1 = damp / rhobar1;
-        psi = sn1 * phibar;
-        phibar = cs1 * phibar;
-    }
-    const double rho = sqrt(rhobar1 * rhobar1 + beta * beta);
-    if (!(rho > 0.0) || !isfinite(rho)) {
-        sc->err = 1;
-        sc->done = 1;
-        return;
-    }
-    const double cs = rhobar1 / rho, sn = beta / rho;
-    const double theta = sn * alpha_new;
-    sc->rhobar = -cs * alpha_new;
-    const double phi = cs * phibar;
-    phibar = sn * phibar;
-    sc->phibar = phibar;
-    const double tau = sn * phi;
-    sc->t1 = phi / rho;
-    sc->t2 = -theta / rho;
-    sc->ddnorm += sc->wnorm2 / (rho * rho);
-    // ||x|| estimate from the LQ factors of the upper bidiagonal R_k
-    const double delta = sc->sn2 * rho, gambar = -sc->cs2 * rho;
-    const double rhs = phi - delta * sc->z;
-    const double zbar = rhs / gambar;
-    sc->xnorm = sqrt(sc->xxnorm + zbar * zbar);
-    const double gamma = sqrt(gambar * gambar + theta * theta);
-    sc->cs2 = gambar / gamma;
-    sc->sn2 = theta / gamma;
-    sc->z = rhs / gamma;
-    sc->xxnorm += sc->z * sc->z;
-    sc->acond = sc->anorm * sqrt(sc->ddnorm);
-    sc->res2 += psi * psi;
-    sc->rnorm = sqrt(phibar * phibar + sc->res2);
-    sc->arnorm = alpha_new * fabs(tau);
-    sc->alpha = alpha_new;
-    sc->itn += 1;
-    sc->pending = 1;
-    if (sc->hist) sc->hist[sc->itn - 1] = sc->rnorm;
-
-    const double eps = DBL_EPSILON;
-    const double bnorm = sc->bnorm, anorm = sc->anorm, xnorm = sc->xnorm, rnorm = sc->rnorm;
-    const double test1 = rnorm / bnorm;
-    const double test2 = sc->arnorm / (anorm * rnorm + eps);
-    const double test3 = 1.0 / (sc->acond + eps);
-    const double t1s = test1 / (1.0 + anorm * xnorm / bnorm);
-    const double rtol = sc->btol + sc->atol * anorm * xnorm / bnorm;
-    int istop = 0;
-    if (test1 <= rtol) istop = 1;
-    else if (test2 <= sc->atol) istop = 2;
-    else if (test3 <= sc->ctol) istop = 3;
-    else if (1.0 + t1s <= 1.0) istop = 4;
-    else if (1.0 + test2 <= 1.0) istop = 5;
-    else if (1.0 + test3 <= 1.0) istop = 6;
-    else if (sc->itn >= sc->itmax) istop = 7;
-    sc->istop = istop;
-    if (!isfinite(rnorm) || !isfinite(sc->arnorm) || !isfinite(sc->t1) || !isfinite(sc->t2)) {
-        sc->err = 1;
-        sc->done = 1;
-    }
 }
 
 // ------------------------------------------------------------------ kernels
