@@ -228,6 +228,45 @@ pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w, doub
 pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev, double w, double lambda,
                                  void *stream);
 
+typedef struct {
+    int32_t tile_rows;        /* G rows per forward work item; 0 = chosen by the autotuner,
+                                 which times the forward phase for 2, 8 and 32 rows */
+    int32_t kblock;           /* iterations per graph launch (<= 0: 8) */
+    int32_t chosen_tile_rows; /* out: the tile used by the call */
+    int32_t kernel_launches;  /* out: kernels launched by the call (graph nodes included) */
+    double tune_ms[4];        /* out: forward-phase time per autotuner candidate (ms) */
+} pdst_batched_opts;
+
+/* Fill *o with the defaults listed above. */
+void pdst_batched_opts_default(pdst_batched_opts *o);
+
+/*
+ * Batched LSQR: nsys independent systems (each its own handle; grid sizes,
+ * row counts and nnz may differ) with nrhs[s] right-hand sides each (1..16),
+ * solved together.  Each phase of an iteration is one persistent launch over a
+ * work list spanning all systems, and each matrix entry read from HBM serves
+ * all right-hand sides of its system.  Each (system, right-hand side) pair runs
+ * its own LSQR recurrence (Paige & Saunders 1982; FP64 scalars) on
+ * A_s = [G_s; w_s L] with damping lambda[s][j], and stops on its own
+ * (atol = btol = tol, conlim = 1e8, itmax iterations at most).
+ *
+ * d_dev[s]: m_s x nrhs[s] FP64 (device), right-hand side fastest.
+ * w[s]: smoothing weight per system.  lambda[s]: nrhs[s] damping values (host).
+ * m_out_dev[s]: n_s x nrhs[s] FP64 (device, caller-owned), right-hand side
+ * fastest.  infos: sum(nrhs) entries, system-major (may be NULL).  dtype:
+ * values and u/v vectors (PDST_F32 / PDST_BF16 use FP32 vectors).  opts may be
+ * NULL (autotuned tile, kblock 8); its out fields are filled when given.
+ * Work space for the batch is allocated on the first call and reused while the
+ * same handles, right-hand-side counts and dtype are passed again.
+ * Synchronous on `stream`.  Errors: PDST_ERR_ARG, PDST_ERR_STATE (dtype not
+ * kept), PDST_ERR_BREAKDOWN, PDST_ERR_OOM, PDST_ERR_CUDA.
+ */
+pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, const int32_t *nrhs,
+                              const double *const *d_dev, const double *w,
+                              const double *const *lambda, int32_t itmax, double tol,
+                              int32_t dtype, double *const *m_out_dev, pdst_lsqr_info *infos,
+                              pdst_batched_opts *opts, void *stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdst_last_error_string(void);
 

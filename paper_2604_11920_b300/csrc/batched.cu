@@ -1,0 +1,785 @@
+// batched.cu -- batched LSQR: many independent systems (each its own handle,
+// sizes may differ) with up to 16 right-hand sides each, solved together.
+//
+// Every phase of an iteration is one persistent launch over a work list that
+// spans all systems (a "segmented" list: each system owns a contiguous range
+// of items).  The right-hand sides of a system share its G: a half-warp holds
+// the 16 right-hand sides in its lanes, so each matrix entry read from HBM is
+// used for all of them (a sparse-times-dense product instead of 16 sparse
+// products).  Each (system, right-hand side) pair keeps its own FP64 LSQR
+// recurrence (Paige & Saunders 1982) with its own damping, and stops on its
+// own; a system whose pairs have all stopped drops out of the work lists.
+//
+// Per iteration: k_bfwd (u-bar <- A v - alpha u, per-item partial norms),
+// k_bred (beta per pair), k_badj (v-bar <- A^T u - beta v), k_bred (alpha and
+// the recurrence per pair), k_bupd (x, w), k_bred (||w||^2).  Reductions sum
+// per-item partials in item order, so results are bit-reproducible.
+//
+// The rows per forward work item are picked by a small autotuner that times
+// the forward phase for a few candidates on the actual batch.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "common.cuh"
+#include "lsqr_dev.cuh"
+
+namespace pdst {
+namespace {
+
+constexpr int BT = 256;      // threads per block
+constexpr int RMAX = 16;     // right-hand sides per system (lanes of a half-warp)
+constexpr int LCOLS = 32;    // columns per stencil / update work item
+
+template <class VT, class ST> struct BSys {
+    int64_t m;
+    int32_t n, nx, ny, nz, R;
+    double w;
+    const int64_t *row_cptr;
+    const int32_t *row_cells;
+    const VT *val;
+    const int64_t *cell_rptr;
+    const int32_t *cell_cnt;
+    const int32_t *cell_rows;
+    const int32_t *cell_order;
+    const VT *valT;
+    ST *U;            // (m + n) x R, right-hand side fastest
+    ST *V;            // n x R
+    double *X, *W;    // n x R
+    const double *d;  // m x R
+    LsqrScalars *sc;  // R
+    int64_t nf;       // forward G-row tiles (then ceil(n / LCOLS) stencil tiles)
+    int32_t active;   // pairs still iterating
+};
+
+enum { PH_INIT = 0, PH_FWD = 1, PH_ADJ_INIT = 2, PH_ADJ = 3, PH_UPD = 4 };
+
+__device__ __forceinline__ int find_sys(const int64_t *__restrict__ beg, int nsys, int64_t it) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (beg[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-lane column state: lane j of each half-warp owns right-hand side j.
+struct Col {
+    bool act;
+    double alpha, beta;
+};
+
+__device__ __forceinline__ Col col_state(const LsqrScalars *sc, int j, int R) {
+    Col c{false, 0.0, 0.0};
+    if (j < R) {
+        const LsqrScalars &s = sc[j];
+        c.act = !(s.done | s.istop);
+        c.alpha = s.alpha;
+        c.beta = s.beta;
+    }
+    return c;
+}
+
+// Laplacian of column j of a strided (rows x R) block.
+template <class AT, class ST>
+__device__ __forceinline__ AT laplace_strided(const ST *__restrict__ x, int64_t jc, int R, int j,
+                                              int nx, int ny, int nz) {
+    const int k = (int)(jc % nz);
+    const int64_t hh = jc / nz;
+    const int ix = (int)(hh % nx), iy = (int)(hh / nx);
+    const int64_t sy = (int64_t)nx * nz;
+    const AT c = (AT)x[jc * R + j];
+    AT s = 0;
+    if (k > 0) s += c - (AT)x[(jc - 1) * R + j];
+    if (k < nz - 1) s += c - (AT)x[(jc + 1) * R + j];
+    if (ix > 0) s += c - (AT)x[(jc - nz) * R + j];
+    if (ix < nx - 1) s += c - (AT)x[(jc + nz) * R + j];
+    if (iy > 0) s += c - (AT)x[(jc - sy) * R + j];
+    if (iy < ny - 1) s += c - (AT)x[(jc + sy) * R + j];
+    return s;
+}
+
+// u-bar = [d; 0], x = w = 0; partials of ||d_j||^2.
+template <class VT, class ST>
+__global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+                                              int64_t nitems, int TR, double *partial) {
+    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int s = find_sys(beg, nsys, it);
+        BSys<VT, ST> &S = sys[s];
+        const int64_t li = it - beg[s];
+        const int R = S.R;
+        double ss = 0.0;
+        if (j < R) {
+            if (li < S.nf) {
+                const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
+                for (int64_t r = r0 + half; r < r1; r += 2) {
+                    const double v = S.d[r * R + j];
+                    S.U[r * R + j] = (ST)v;
+                    ss += v * v;
+                }
+            } else {
+                const int64_t c0 = (li - S.nf) * LCOLS;
+                const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
+                for (int64_t c = c0 + half; c < c1; c += 2) {
+                    S.U[(S.m + c) * R + j] = (ST)0;
+                    S.V[c * R + j] = (ST)0;
+                    S.X[c * R + j] = 0.0;
+                    S.W[c * R + j] = 0.0;
+                }
+            }
+        }
+        ss += __shfl_xor_sync(FULL, ss, 16);
+        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+    }
+}
+
+// Forward phase: G rows (half-warp per row, lanes = right-hand sides) and the
+// w L rows (stencil tiles) of every active system.
+template <class VT, class ST>
+__global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+                                             int64_t nitems, int TR, double *partial) {
+    using AT = ST;
+    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int s = find_sys(beg, nsys, it);
+        const BSys<VT, ST> &S = sys[s];
+        const int64_t li = it - beg[s];
+        double ss = 0.0;
+        if (S.active > 0) {
+            const int R = S.R, nz = S.nz;
+            const int jj = j < R ? j : 0;
+            const Col c = col_state(S.sc, j, R);
+            const AT ia = c.alpha > 0.0 ? (AT)(1.0 / c.alpha) : (AT)0;
+            const AT cu = c.beta > 0.0 ? (AT)(c.alpha / c.beta) : (AT)0;
+            if (li < S.nf) {
+                const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
+                for (int64_t r = r0 + half; r < r1; r += 2) {
+                    const int64_t e0 = __ldg(S.row_cptr + r), e1 = __ldg(S.row_cptr + r + 1);
+                    AT acc = 0;
+                    for (int64_t e = e0; e < e1; ++e) {
+                        const int h = __ldg(S.row_cells + e);
+                        const VT *v = S.val + e * nz;
+                        const ST *vb = S.V + (int64_t)h * nz * R + jj;
+                        if ((nz & 3) == 0) {
+                            for (int k = 0; k < nz; k += 4) {
+                                typename Wide<VT>::T q[4];
+                                Pack4<VT>::ld(v + k, q);
+                                acc += (AT)q[0] * (AT)vb[(k + 0) * R] + (AT)q[1] * (AT)vb[(k + 1) * R] +
+                                       (AT)q[2] * (AT)vb[(k + 2) * R] + (AT)q[3] * (AT)vb[(k + 3) * R];
+                            }
+                        } else {
+                            for (int k = 0; k < nz; ++k) acc += (AT)widen(v[k]) * (AT)vb[k * R];
+                        }
+                    }
+                    if (c.act) {
+                        const AT u = acc * ia - cu * S.U[r * R + j];
+                        S.U[r * R + j] = u;
+                        ss += (double)u * (double)u;
+                    }
+                }
+            } else {
+                const int64_t c0 = (li - S.nf) * LCOLS;
+                const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
+                const AT wsm = (AT)S.w;
+                for (int64_t jc = c0 + half; jc < c1; jc += 2) {
+                    const AT lap = laplace_strided<AT, ST>(S.V, jc, R, jj, S.nx, S.ny, nz);
+                    if (c.act) {
+                        ST *up = S.U + (S.m + jc) * R + j;
+                        const AT u = wsm * lap * ia - cu * *up;
+                        *up = u;
+                        ss += (double)u * (double)u;
+                    }
+                }
+            }
+        }
+        ss += __shfl_xor_sync(FULL, ss, 16);
+        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+    }
+}
+
+// Adjoint phase: work item = (cell, group of up to four depths) of one
+// system, cells longest first; the two half-warps take alternate rows of the
+// cell, lanes = right-hand sides.
+template <class VT, class ST>
+__global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+                                             int64_t nitems, int init, double *partial) {
+    using AT = ST;
+    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int s = find_sys(beg, nsys, it);
+        const BSys<VT, ST> &S = sys[s];
+        const int64_t li = it - beg[s];
+        double ss = 0.0;
+        if (S.active > 0) {
+            const int R = S.R, nz = S.nz;
+            const int jj = j < R ? j : 0;
+            const Col c = col_state(S.sc, j, R);
+            const bool upd = c.act && (init || c.beta > 0.0);
+            const AT ib = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
+            const AT cv = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
+            const int kg = (nz + 3) >> 2;
+            const int h = __ldg(S.cell_order + li / kg);
+            const int k0 = 4 * (int)(li % kg);
+            const int nk = nz - k0 < 4 ? nz - k0 : 4;
+            const int64_t c0 = __ldg(S.cell_rptr + h);
+            const int cnt = __ldg(S.cell_cnt + h);
+            const VT *vb = S.valT + (int64_t)nz * c0 + (int64_t)k0 * cnt;
+            const int32_t *rows = S.cell_rows + c0;
+            AT acc[4] = {0, 0, 0, 0};
+            for (int q = half; q < cnt; q += 2) {
+                const int r = __ldg(rows + q);
+                const AT ur = (AT)S.U[(int64_t)r * R + jj];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (t < nk) acc[t] += (AT)ldval(vb + (int64_t)t * cnt + q) * ur;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], 16);
+            if (half == 0 && upd) {
+                const AT wsm = (AT)S.w;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (t < nk) {
+                        const int64_t jc = (int64_t)h * nz + k0 + t;
+                        const AT sv = acc[t] + wsm * laplace_strided<AT, ST>(S.U + S.m * R, jc, R, j,
+                                                                             S.nx, S.ny, nz);
+                        ST *vp = S.V + jc * R + j;
+                        const AT v = init ? sv * ib : sv * ib - cv * *vp;
+                        *vp = v;
+                        ss += (double)v * (double)v;
+                    }
+                }
+            }
+        }
+        ss += __shfl_xor_sync(FULL, ss, 16);
+        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+    }
+}
+
+// x += t1 w, w = v + t2 w (FP64) for pairs with a pending update; ||w||^2.
+template <class VT, class ST>
+__global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+                                             int64_t nitems, double *partial) {
+    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int s = find_sys(beg, nsys, it);
+        const BSys<VT, ST> &S = sys[s];
+        const int64_t li = it - beg[s];
+        double ss = 0.0;
+        if (j < S.R) {
+            const LsqrScalars &sc = S.sc[j];
+            const int pend = sc.pending;
+            if (pend) {
+                const double ia = sc.alpha > 0.0 ? 1.0 / sc.alpha : 0.0;
+                const double t1 = sc.t1, t2 = sc.t2;
+                const int64_t c0 = li * LCOLS, c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
+                for (int64_t c = c0 + half; c < c1; c += 2) {
+                    const int64_t i = c * S.R + j;
+                    const double v = (double)S.V[i] * ia;
+                    double w = S.W[i];
+                    if (pend == 2) {
+                        w = v;
+                    } else {
+                        S.X[i] += t1 * w;
+                        w = v + t2 * w;
+                    }
+                    S.W[i] = w;
+                    ss += w * w;
+                }
+            }
+        }
+        ss += __shfl_xor_sync(FULL, ss, 16);
+        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+    }
+}
+
+// One block per system, one thread per right-hand side: sum the phase's
+// per-item partials in item order and advance that pair's scalars; thread 0
+// then counts the pairs still iterating.
+template <class VT, class ST>
+__global__ void k_bred(BSys<VT, ST> *sys, const int64_t *beg, const double *partial, int phase,
+                       int *active_out) {
+    const int s = blockIdx.x, j = threadIdx.x;
+    BSys<VT, ST> &S = sys[s];
+    if (j < S.R) {
+        LsqrScalars *sc = S.sc + j;
+        const bool frozen = (phase == PH_UPD) ? !sc->pending : (sc->done | sc->istop) != 0;
+        if (!frozen) {
+            double t = 0.0;
+            for (int64_t i = beg[s]; i < beg[s + 1]; ++i) t += partial[i * RMAX + j];
+            if (phase == PH_INIT) {
+                const double b = sqrt(t);
+                sc->beta = b;
+                sc->bnorm = b;
+                sc->rnorm = b;
+                sc->phibar = b;
+                if (!isfinite(b)) sc->err = 1;
+                if (!(b > 0.0) || !isfinite(b)) sc->done = 1;
+            } else if (phase == PH_FWD) {
+                const double b = sqrt(t);
+                if (!isfinite(b)) {
+                    sc->err = 1;
+                    sc->done = 1;
+                }
+                sc->beta = b;
+            } else if (phase == PH_ADJ_INIT || phase == PH_ADJ) {
+                const double an = (phase == PH_ADJ && !(sc->beta > 0.0)) ? sc->alpha : sqrt(t);
+                if (!isfinite(an)) {
+                    sc->err = 1;
+                    sc->done = 1;
+                } else if (phase == PH_ADJ_INIT) {
+                    sc->alpha = an;
+                    sc->rhobar = an;
+                    sc->arnorm = an * sc->beta;
+                    sc->pending = 2;
+                    if (!(sc->arnorm > 0.0)) sc->done = 1;
+                } else {
+                    lsqr_step(sc, an);
+                }
+            } else {
+                sc->wnorm2 = t;
+                sc->pending = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (j == 0) {
+        int a = 0;
+        for (int k = 0; k < S.R; ++k) a += !(S.sc[k].done | S.sc[k].istop);
+        S.active = a;
+        active_out[s] = a;
+    }
+}
+
+// ------------------------------------------------------------------ driver
+
+struct BatchKey {
+    std::vector<uint64_t> hs;   // handle uids
+    std::vector<int32_t> nrhs;
+    int dtype;
+    bool operator<(const BatchKey &o) const {
+        return std::tie(hs, nrhs, dtype) < std::tie(o.hs, o.nrhs, o.dtype);
+    }
+};
+
+struct BatchWork {
+    BatchKey key;
+    int TR = 0;
+    bool tuned = false;
+    std::vector<DevBuf *> bufs;
+    DevBuf desc, scal, partial, fbeg, abeg, ubeg, active;
+    int *h_active = nullptr;
+    LsqrScalars *h_scal = nullptr;
+    int64_t nf_items = 0, na_items = 0, nu_items = 0;
+    std::vector<int64_t> hf, ha, hu;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<double> tune_ms;
+    ~BatchWork() {
+        for (auto *b : bufs) delete b;
+        for (auto &g : graphs)
+            if (g.second) cudaGraphExecDestroy(g.second);
+        if (h_active) cudaFreeHost(h_active);
+        if (h_scal) cudaFreeHost(h_scal);
+    }
+};
+
+static std::mutex g_batch_mutex;
+static BatchWork *g_batch = nullptr;   // the most recent batch (reused when identical)
+
+template <class K> static unsigned bgrid(K kernel, int device, int64_t items) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)num_sms(device) * per_sm;
+    int64_t need = (items + (BT / 32) - 1) / (BT / 32);
+    if (need < 1) need = 1;
+    return (unsigned)(g < need ? g : need);
+}
+
+template <class VT, class ST> struct Batched {
+    using Sys = BSys<VT, ST>;
+
+    // Forward item layout for TR rows per item.
+    static void layout_fwd(const std::vector<pdst_handle *> &hs, int TR, std::vector<int64_t> &beg,
+                           std::vector<int64_t> &nf) {
+        beg.assign(hs.size() + 1, 0);
+        nf.resize(hs.size());
+        for (size_t s = 0; s < hs.size(); ++s) {
+            nf[s] = (hs[s]->m + TR - 1) / TR;
+            const int64_t nl = ((int64_t)hs[s]->n + LCOLS - 1) / LCOLS;
+            beg[s + 1] = beg[s] + nf[s] + nl;
+        }
+    }
+
+    static pdst_status prepare(BatchWork *bw, const std::vector<pdst_handle *> &hs,
+                               const int32_t *nrhs, int dtype, int TR, cudaStream_t s) {
+        const int nsys = (int)hs.size();
+        std::vector<Sys> d(nsys);
+        std::vector<int64_t> nf;
+        layout_fwd(hs, TR, bw->hf, nf);
+        bw->ha.assign(nsys + 1, 0);
+        bw->hu.assign(nsys + 1, 0);
+        for (int i = 0; i < nsys; ++i) {
+            pdst_handle *h = hs[i];
+            const int kg = (h->nz + 3) / 4;
+            bw->ha[i + 1] = bw->ha[i] + (int64_t)h->H * kg;
+            bw->hu[i + 1] = bw->hu[i] + ((int64_t)h->n + LCOLS - 1) / LCOLS;
+        }
+        bw->nf_items = bw->hf[nsys];
+        bw->na_items = bw->ha[nsys];
+        bw->nu_items = bw->hu[nsys];
+        const int64_t maxitems = std::max(bw->nf_items, std::max(bw->na_items, bw->nu_items));
+        // (re)allocate vectors only on a new batch
+        if (bw->bufs.empty()) {
+            for (int i = 0; i < nsys; ++i) {
+                pdst_handle *h = hs[i];
+                const int R = nrhs[i];
+                DevBuf *U = new DevBuf, *V = new DevBuf, *X = new DevBuf, *W = new DevBuf;
+                bw->bufs.insert(bw->bufs.end(), {U, V, X, W});
+                PDST_TRY(U->alloc(sizeof(ST) * (h->m + h->n) * R));
+                PDST_TRY(V->alloc(sizeof(ST) * (int64_t)h->n * R));
+                PDST_TRY(X->alloc(sizeof(double) * (int64_t)h->n * R));
+                PDST_TRY(W->alloc(sizeof(double) * (int64_t)h->n * R));
+            }
+            PDST_TRY(bw->scal.alloc(sizeof(LsqrScalars) * nsys * RMAX));
+            PDST_TRY(bw->desc.alloc(sizeof(Sys) * nsys));
+            PDST_TRY(bw->active.alloc(sizeof(int) * nsys));
+            PDST_TRY(bw->abeg.alloc(sizeof(int64_t) * (nsys + 1)));
+            PDST_TRY(bw->ubeg.alloc(sizeof(int64_t) * (nsys + 1)));
+            PDST_CUDA(cudaMallocHost(&bw->h_active, sizeof(int) * nsys));
+            PDST_CUDA(cudaMallocHost(&bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX));
+        }
+        PDST_TRY(bw->partial.alloc(sizeof(double) * RMAX * std::max<int64_t>(maxitems, 1)));
+        PDST_TRY(bw->fbeg.alloc(sizeof(int64_t) * (nsys + 1)));
+        LsqrScalars *scd = bw->scal.as<LsqrScalars>();
+        for (int i = 0; i < nsys; ++i) {
+            pdst_handle *h = hs[i];
+            Sys &q = d[i];
+            q.m = h->m;
+            q.n = h->n;
+            q.nx = h->grid.nx;
+            q.ny = h->grid.ny;
+            q.nz = h->nz;
+            q.R = nrhs[i];
+            q.row_cptr = h->row_cptr.as<int64_t>();
+            q.row_cells = h->row_cells.as<int32_t>();
+            q.val = h->vals[dtype].csr.as<VT>();
+            q.cell_rptr = h->cell_rptr.as<int64_t>();
+            q.cell_cnt = h->cell_cnt.as<int32_t>();
+            q.cell_rows = h->cell_rows.as<int32_t>();
+            q.cell_order = h->cell_order.as<int32_t>();
+            q.valT = h->vals[dtype].csc.as<VT>();
+            q.U = bw->bufs[4 * i]->as<ST>();
+            q.V = bw->bufs[4 * i + 1]->as<ST>();
+            q.X = bw->bufs[4 * i + 2]->as<double>();
+            q.W = bw->bufs[4 * i + 3]->as<double>();
+            q.sc = scd + (size_t)i * RMAX;
+            q.nf = nf[i];
+            q.active = 0;
+        }
+        bw->TR = TR;
+        PDST_CUDA(cudaMemcpyAsync(bw->desc.p, d.data(), sizeof(Sys) * nsys, cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(bw->fbeg.p, bw->hf.data(), sizeof(int64_t) * (nsys + 1),
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(bw->abeg.p, bw->ha.data(), sizeof(int64_t) * (nsys + 1),
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(bw->ubeg.p, bw->hu.data(), sizeof(int64_t) * (nsys + 1),
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        return PDST_OK;
+    }
+
+    // per-call inputs: right-hand sides and scalars
+    static pdst_status load_inputs(BatchWork *bw, int nsys, const double *const *d_dev,
+                                   const std::vector<LsqrScalars> &init, cudaStream_t s) {
+        std::vector<Sys> d(nsys);
+        PDST_CUDA(cudaMemcpyAsync(d.data(), bw->desc.p, sizeof(Sys) * nsys, cudaMemcpyDeviceToHost, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nsys; ++i) {
+            d[i].d = d_dev[i];
+            d[i].w = init[(size_t)i * RMAX].w_smooth;
+            d[i].active = d[i].R;
+        }
+        PDST_CUDA(cudaMemcpyAsync(bw->desc.p, d.data(), sizeof(Sys) * nsys, cudaMemcpyHostToDevice, s));
+        std::copy(init.begin(), init.end(), bw->h_scal);
+        PDST_CUDA(cudaMemcpyAsync(bw->scal.p, bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX,
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        return PDST_OK;
+    }
+
+    static void launch_iter(BatchWork *bw, int nsys, int device, cudaStream_t s) {
+        Sys *sys = bw->desc.as<Sys>();
+        double *part = bw->partial.as<double>();
+        k_bfwd<VT, ST><<<bgrid(k_bfwd<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
+            sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_FWD,
+                                           bw->active.as<int>());
+        k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
+            sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ,
+                                           bw->active.as<int>());
+        k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
+            sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
+                                           bw->active.as<int>());
+    }
+
+    static pdst_status start(BatchWork *bw, int nsys, int device, cudaStream_t s) {
+        Sys *sys = bw->desc.as<Sys>();
+        double *part = bw->partial.as<double>();
+        k_binit<VT, ST><<<bgrid(k_binit<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
+            sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_INIT,
+                                           bw->active.as<int>());
+        k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
+            sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ_INIT,
+                                           bw->active.as<int>());
+        k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
+            sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
+        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
+                                           bw->active.as<int>());
+        PDST_CUDA(cudaGetLastError());
+        return PDST_OK;
+    }
+
+    // Time the forward phase for each candidate tile and keep the fastest.
+    static pdst_status autotune(BatchWork *bw, const std::vector<pdst_handle *> &hs,
+                                const int32_t *nrhs, int dtype, const double *const *d_dev,
+                                const std::vector<LsqrScalars> &init, int device, cudaStream_t s) {
+        const int cands[] = {2, 8, 32};
+        double best = 1e300;
+        int best_tr = 8;
+        bw->tune_ms.clear();
+        const int nsys = (int)hs.size();
+        cudaEvent_t e0, e1;
+        PDST_CUDA(cudaEventCreate(&e0));
+        PDST_CUDA(cudaEventCreate(&e1));
+        for (int tr : cands) {
+            PDST_TRY(prepare(bw, hs, nrhs, dtype, tr, s));
+            PDST_TRY(load_inputs(bw, nsys, d_dev, init, s));
+            PDST_TRY(start(bw, nsys, device, s));
+            Sys *sys = bw->desc.as<Sys>();
+            float ms = 0.f, tot = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                k_bfwd<VT, ST><<<bgrid(k_bfwd<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
+                    sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
+                    bw->partial.as<double>());
+                cudaEventRecord(e1, s);
+                PDST_CUDA(cudaEventSynchronize(e1));
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;
+            }
+            bw->tune_ms.push_back(tot / 2);
+            if (tot / 2 < best) {
+                best = tot / 2;
+                best_tr = tr;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return prepare(bw, hs, nrhs, dtype, best_tr, s);
+    }
+
+    static pdst_status run(BatchWork *bw, const std::vector<pdst_handle *> &hs, const int32_t *nrhs,
+                           int dtype, const double *const *d_dev, const std::vector<LsqrScalars> &init,
+                           int kblock, int tile_rows, double *const *m_out, cudaStream_t s,
+                           int &launches) {
+        const int nsys = (int)hs.size();
+        const int device = hs[0]->device;
+        // tile_rows > 0: use it; 0: use the autotuned tile (tune once per batch)
+        const bool want_tune = tile_rows == 0 && !bw->tuned;
+        const bool want_fixed = tile_rows > 0 && (tile_rows != bw->TR || bw->tuned);
+        if (want_tune || want_fixed || bw->TR == 0) {
+            for (auto &g : bw->graphs)
+                if (g.second) cudaGraphExecDestroy(g.second);
+            bw->graphs.clear();
+            if (tile_rows > 0) {
+                PDST_TRY(prepare(bw, hs, nrhs, dtype, tile_rows, s));
+                bw->tuned = false;
+            } else {
+                PDST_TRY(autotune(bw, hs, nrhs, dtype, d_dev, init, device, s));
+                bw->tuned = true;
+            }
+        }
+        PDST_TRY(load_inputs(bw, nsys, d_dev, init, s));
+        PDST_TRY(start(bw, nsys, device, s));
+        launches += 6;
+        cudaGraphExec_t exec = nullptr;
+        auto it = bw->graphs.find(kblock);
+        if (it != bw->graphs.end()) {
+            exec = it->second;
+        } else {
+            cudaStream_t cs;
+            PDST_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int i = 0; i < kblock; ++i) launch_iter(bw, nsys, device, cs);
+                e = cudaStreamEndCapture(cs, &g);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                set_error("batched LSQR graph capture: %s", cudaGetErrorString(e));
+                return PDST_ERR_CUDA;
+            }
+            bw->graphs[kblock] = exec;
+        }
+        for (;;) {
+            PDST_CUDA(cudaMemcpyAsync(bw->h_active, bw->active.p, sizeof(int) * nsys,
+                                      cudaMemcpyDeviceToHost, s));
+            PDST_CUDA(cudaStreamSynchronize(s));
+            int any = 0;
+            for (int i = 0; i < nsys; ++i) any += bw->h_active[i];
+            if (!any) break;
+            PDST_CUDA(cudaGraphLaunch(exec, s));
+            launches += 6 * kblock;
+        }
+        for (int i = 0; i < nsys; ++i)
+            PDST_CUDA(cudaMemcpyAsync(m_out[i], bw->bufs[4 * i + 2]->p,
+                                      sizeof(double) * (int64_t)hs[i]->n * nrhs[i],
+                                      cudaMemcpyDeviceToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(bw->h_scal, bw->scal.p, sizeof(LsqrScalars) * nsys * RMAX,
+                                  cudaMemcpyDeviceToHost, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        return PDST_OK;
+    }
+};
+
+}  // namespace
+}  // namespace pdst
+
+using namespace pdst;
+
+extern "C" void pdst_batched_opts_default(pdst_batched_opts *o) {
+    if (!o) return;
+    o->tile_rows = 0;
+    o->kblock = 8;
+    o->chosen_tile_rows = 0;
+    o->kernel_launches = 0;
+    for (int i = 0; i < 4; ++i) o->tune_ms[i] = 0.0;
+}
+
+extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, const int32_t *nrhs,
+                                         const double *const *d_dev, const double *w,
+                                         const double *const *lambda, int32_t itmax, double tol,
+                                         int32_t dtype, double *const *m_out_dev,
+                                         pdst_lsqr_info *infos, pdst_batched_opts *opts,
+                                         void *stream) {
+    PDST_CHECK_ARG(nsys >= 1 && hs && nrhs && d_dev && w && lambda && m_out_dev,
+                   "pdst_lsqr_batched: NULL argument or nsys < 1");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_lsqr_batched: unknown dtype");
+    PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr_batched: itmax must be >= 0");
+    PDST_CHECK_ARG(std::isfinite(tol) && tol >= 0.0, "pdst_lsqr_batched: tol must be >= 0");
+    std::vector<pdst_handle *> H(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        PDST_CHECK_ARG(hs[i] != nullptr, "pdst_lsqr_batched: handle %d is NULL", i);
+        PDST_CHECK_ARG(nrhs[i] >= 1 && nrhs[i] <= RMAX,
+                       "pdst_lsqr_batched: nrhs[%d] must be in 1..%d", i, RMAX);
+        PDST_CHECK_ARG(hs[i]->device == hs[0]->device,
+                       "pdst_lsqr_batched: all handles must be on one device");
+        PDST_CHECK_ARG(hs[i]->m == 0 || d_dev[i], "pdst_lsqr_batched: d[%d] is NULL", i);
+        PDST_CHECK_ARG(m_out_dev[i] && lambda[i], "pdst_lsqr_batched: NULL output or lambda");
+        PDST_CHECK_ARG(std::isfinite(w[i]) && w[i] >= 0.0, "pdst_lsqr_batched: bad w[%d]", i);
+        for (int j = 0; j < nrhs[i]; ++j)
+            PDST_CHECK_ARG(std::isfinite(lambda[i][j]) && lambda[i][j] >= 0.0,
+                           "pdst_lsqr_batched: bad lambda[%d][%d]", i, j);
+        if (!hs[i]->vals[dtype].present) {
+            set_error("pdst_lsqr_batched: values of dtype %d were not kept in handle %d", dtype, i);
+            return PDST_ERR_STATE;
+        }
+        H[i] = hs[i];
+    }
+    pdst_batched_opts local;
+    pdst_batched_opts_default(&local);
+    if (opts) local = *opts;
+    const int kblock = local.kblock > 0 ? local.kblock : 8;
+    PDST_CHECK_ARG(kblock <= 256, "pdst_lsqr_batched: kblock must be <= 256");
+    PDST_CHECK_ARG(local.tile_rows >= 0 && local.tile_rows <= 4096,
+                   "pdst_lsqr_batched: tile_rows out of range");
+
+    std::vector<LsqrScalars> init((size_t)nsys * RMAX);
+    for (int i = 0; i < nsys; ++i)
+        for (int j = 0; j < RMAX; ++j) {
+            LsqrScalars &q = init[(size_t)i * RMAX + j];
+            q = LsqrScalars{};
+            q.cs2 = -1.0;
+            q.damp = j < nrhs[i] ? lambda[i][j] : 0.0;
+            q.atol = tol;
+            q.btol = tol;
+            q.ctol = 1e-8;
+            q.w_smooth = w[i];
+            q.itmax = itmax;
+            if (j >= nrhs[i] || itmax == 0) q.done = 1;
+        }
+
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchKey key{std::vector<uint64_t>(nsys), std::vector<int32_t>(nrhs, nrhs + nsys), dtype};
+    for (int i = 0; i < nsys; ++i) key.hs[i] = hs[i]->uid;
+    if (!g_batch || g_batch->key < key || key < g_batch->key) {
+        delete g_batch;
+        g_batch = new BatchWork();
+        g_batch->key = key;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    pdst_status st;
+    if (dtype == PDST_F64)
+        st = Batched<double, double>::run(g_batch, H, nrhs, dtype, d_dev, init, kblock,
+                                          local.tile_rows, m_out_dev, s, launches);
+    else if (dtype == PDST_F32)
+        st = Batched<float, float>::run(g_batch, H, nrhs, dtype, d_dev, init, kblock,
+                                        local.tile_rows, m_out_dev, s, launches);
+    else
+        st = Batched<__nv_bfloat16, float>::run(g_batch, H, nrhs, dtype, d_dev, init, kblock,
+                                                local.tile_rows, m_out_dev, s, launches);
+    if (st != PDST_OK) {
+        delete g_batch;
+        g_batch = nullptr;
+        return st;
+    }
+    if (opts) {
+        opts->chosen_tile_rows = g_batch->TR;
+        opts->kernel_launches = launches;
+        for (size_t i = 0; i < 4; ++i)
+            opts->tune_ms[i] = i < g_batch->tune_ms.size() ? g_batch->tune_ms[i] : 0.0;
+    }
+    bool err = false;
+    size_t k = 0;
+    for (int i = 0; i < nsys; ++i)
+        for (int j = 0; j < nrhs[i]; ++j) {
+            const LsqrScalars &c = g_batch->h_scal[(size_t)i * RMAX + j];
+            err |= c.err != 0;
+            if (infos) {
+                pdst_lsqr_info &f = infos[k++];
+                f = pdst_lsqr_info{};
+                f.iters = c.itn;
+                f.istop = c.istop;
+                f.rnorm = c.rnorm;
+                f.arnorm = c.arnorm;
+                f.anorm = c.anorm;
+                f.acond = c.acond;
+                f.xnorm = c.xnorm;
+                f.bnorm = c.bnorm;
+            }
+        }
+    if (err) {
+        set_error("pdst_lsqr_batched: non-finite value in a recurrence");
+        return PDST_ERR_BREAKDOWN;
+    }
+    return PDST_OK;
+}

@@ -19,6 +19,7 @@
 //   row_ptr, col, col_ptr, row_idx             element indices (PDST_FMT_ELEMENT)
 // with nnz = nz * U and the CSC of column j = h*nz + k starting at
 // nz*cell_rptr[h] + k*cnt[h].
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -619,7 +620,9 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
     PDST_CHECK_ARG((dtypes & ~7u) == 0, "pdst_build_G: unknown value dtype bits");
     PDST_CHECK_ARG((formats & ~3u) == 0, "pdst_build_G: unknown format bits");
 
+    static std::atomic<uint64_t> next_uid{1};
     pdst_handle *h = new pdst_handle();
+    h->uid = next_uid.fetch_add(1);
     cudaGetDevice(&h->device);
     h->grid = *grid;
     h->m = n_paths;

@@ -118,6 +118,7 @@ inline int num_sms(int device) {
 }  // namespace pdst
 
 struct pdst_handle {
+    uint64_t uid = 0;       // unique per handle in this process (never reused)
     int device = 0;
     pdst_grid grid{};
     int64_t m = 0;          // rows of G

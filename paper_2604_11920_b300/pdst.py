@@ -51,6 +51,12 @@ class LsqrOpts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p)]
 
 
+class BatchedOpts(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("kblock", ctypes.c_int32),
+                ("chosen_tile_rows", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * 4)]
+
+
 class LsqrInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("istop", ctypes.c_int32),
                 ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
@@ -86,6 +92,9 @@ SIGNATURES = {
     "pdst_lsqr_noalloc": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
                                  ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_set_col_scaling": (_i32, [_vp, _vp, _d, _d, _vp]),
+    "pdst_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
+    "pdst_lsqr_batched": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _i32, _d, _i32, _vp,
+                                 ctypes.POINTER(LsqrInfo), ctypes.POINTER(BatchedOpts), _vp]),
     "pdst_last_error_string": (ctypes.c_char_p, []),
     "pdst_version": (_i32, []),
 }
@@ -270,3 +279,40 @@ def build_G_problem(p, **kw) -> Handle:
     """pdst_build_G for a generator problem (see synth.py)."""
     return build_G(p.nx, p.ny, p.nz, p.dx_km, p.dz_km, p.ctrl, p.row_period, p.n_periods,
                    p.kdz, **kw)
+
+
+def lsqr_batched(handles, ds, w, lams, itmax, tol, dtype="f32", tile_rows=0, kblock=8,
+                 m_outs=None, stream=None):
+    """pdst_lsqr_batched.  ds[s]: (m_s, R_s) float64 CUDA tensors (right-hand
+    sides in columns); lams[s]: R_s damping values.  Returns (m_outs, infos,
+    opts) with m_outs[s] of shape (n_s, R_s)."""
+    import torch
+    lib = load()
+    nsys = len(handles)
+    R = [int(d.shape[1]) for d in ds]
+    if m_outs is None:
+        m_outs = [torch.empty((h.n, r), dtype=torch.float64, device=ds[0].device)
+                  for h, r in zip(handles, R)]
+    hs = (ctypes.c_void_p * nsys)(*[h.ptr.value if isinstance(h.ptr, ctypes.c_void_p) else h.ptr
+                                    for h in handles])
+    nr = (ctypes.c_int32 * nsys)(*R)
+    dp = (ctypes.c_void_p * nsys)(*[_dev_ptr(d, h.m * r, torch.float64, "d").value
+                                    for d, h, r in zip(ds, handles, R)])
+    mp = (ctypes.c_void_p * nsys)(*[_dev_ptr(m, h.n * r, torch.float64, "m_out").value
+                                    for m, h, r in zip(m_outs, handles, R)])
+    wv = (ctypes.c_double * nsys)(*[float(x) for x in w])
+    lam_arrs = [(ctypes.c_double * r)(*[float(x) for x in l]) for l, r in zip(lams, R)]
+    lp = (ctypes.c_void_p * nsys)(*[ctypes.cast(a, ctypes.c_void_p).value for a in lam_arrs])
+    infos = (LsqrInfo * sum(R))()
+    o = BatchedOpts()
+    lib.pdst_batched_opts_default(ctypes.byref(o))
+    o.tile_rows, o.kblock = int(tile_rows), int(kblock)
+    _check(lib.pdst_lsqr_batched(nsys, hs, nr, dp, wv, lp, int(itmax), float(tol), DTYPES[dtype],
+                                 mp, infos, ctypes.byref(o), _stream(stream)))
+    out_infos, k = [], 0
+    for r in R:
+        out_infos.append([infos[k + i].as_dict() for i in range(r)])
+        k += r
+    return m_outs, out_infos, {"chosen_tile_rows": o.chosen_tile_rows,
+                               "kernel_launches": o.kernel_launches,
+                               "tune_ms": list(o.tune_ms)}

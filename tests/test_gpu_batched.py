@@ -1,0 +1,108 @@
+"""Batched LSQR (one persistent launch per phase over all systems, the
+right-hand sides of a system sharing its G) against single-system LSQR and
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_11920_b300 import pdst, synth
+from gpu_util import rel, require_cuda, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch():
+    """Three uneven systems (one with nz not a multiple of 4) and their
+    right-hand sides: checkerboards of several block sizes and noisy data."""
+    probs = [synth.custom(12, 10, 8, 14, 6, bend=0.15, seed=31, w=1.0, lam=0.1),
+             synth.custom(9, 13, 4, 18, 9, bend=0.1, seed=32, w=2.0, lam=0.05),
+             synth.custom(7, 6, 3, 10, 4, bend=0.15, seed=33, w=0.5, lam=0.2)]
+    nrhs = [3, 16, 1]
+    out = []
+    for p, R in zip(probs, nrhs):
+        G = oracle.build_G_problem(p)
+        cols, lams = [], []
+        for j in range(R):
+            b = 2 + (j % 5)
+            m = synth.checkerboard(p.nx, p.ny, p.nz, b, 0.05) * (1 if j % 2 == 0 else -1)
+            cols.append(oracle.rhs_for(p, G, m_model=m, noise=synth.rhs_noise(p.seed, p.m_rows, j)))
+            lams.append(float(np.logspace(-3, 0, R)[j]) if R > 1 else p.lam)
+        out.append((p, G, np.stack(cols, axis=1), lams))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    require_cuda()
+    b = small_batch()
+    hs = [pdst.build_G_problem(p, dtypes=("f64", "f32", "bf16")) for p, _, _, _ in b]
+    return b, hs
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_fixed_k_matches_single_system_solves(batch, k):
+    b, hs = batch
+    ds = [to_dev(D) for _, _, D, _ in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, _, _, _ in b],
+                                       [l for _, _, _, l in b], k, 0.0, dtype="f64", tile_rows=4)
+    for (p, G, D, lams), h, mo, inf in zip(b, hs, outs, infos):
+        for j in range(D.shape[1]):
+            single = h.lsqr(to_dev(D[:, j]), p.w, lams[j], k, 0.0, fmt="blocked", conlim=1e8)
+            assert inf[j]["iters"] == single.info["iters"] == k
+            assert rel(mo[:, j].cpu().numpy(), single.m.cpu().numpy()) < 1e-10
+
+
+def test_converged_columns_match_oracle(batch):
+    b, hs = batch
+    ds = [to_dev(D) for _, _, D, _ in b]
+    outs, infos, opts = pdst.lsqr_batched(hs, ds, [p.w for p, _, _, _ in b],
+                                          [l for _, _, _, l in b], 20000, 1e-9, dtype="f64")
+    assert opts["chosen_tile_rows"] in (2, 8, 32)
+    assert sum(t > 0 for t in opts["tune_ms"]) == 3
+    for (p, G, D, lams), mo, inf in zip(b, outs, infos):
+        GT = oracle.transpose(G)
+        for j in sorted({0, D.shape[1] - 1, D.shape[1] // 2}):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, lams[j], D[:, j], atol=1e-12,
+                              btol=1e-12, itmax=50000)
+            assert inf[j]["istop"] in (1, 2)
+            assert rel(mo[:, j].cpu().numpy(), ref.x) <= 1e-4
+
+
+def test_fp32_batched_close_to_fp32_single(batch):
+    b, hs = batch
+    ds = [to_dev(D) for _, _, D, _ in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, _, _, _ in b],
+                                       [l for _, _, _, l in b], 20000, 1e-6, dtype="f32")
+    for (p, G, D, lams), h, mo, inf in zip(b, hs, outs, infos):
+        for j in (0, D.shape[1] - 1):
+            single = h.lsqr(to_dev(D[:, j]), p.w, lams[j], 20000, 1e-6, dtype="f32", fmt="blocked")
+            ref = h.lsqr(to_dev(D[:, j]), p.w, lams[j], 20000, 1e-10, dtype="f64")
+            e_b = rel(mo[:, j].cpu().numpy(), ref.m.cpu().numpy())
+            e_s = rel(single.m.cpu().numpy(), ref.m.cpu().numpy())
+            assert e_b <= 2 * e_s + 1e-4, (e_b, e_s)
+
+
+def test_repeat_call_is_bit_identical_and_itmax_zero(batch):
+    b, hs = batch
+    ds = [to_dev(D) for _, _, D, _ in b]
+    args = ([p.w for p, _, _, _ in b], [l for _, _, _, l in b])
+    o1, _, _ = pdst.lsqr_batched(hs, ds, *args, 50, 0.0, dtype="f32", tile_rows=8)
+    o2, _, _ = pdst.lsqr_batched(hs, ds, *args, 50, 0.0, dtype="f32", tile_rows=8)
+    for a, c in zip(o1, o2):
+        assert np.array_equal(a.cpu().numpy(), c.cpu().numpy())
+    o3, i3, _ = pdst.lsqr_batched(hs, ds, *args, 0, 1e-6, dtype="f32")
+    assert all(not m.cpu().numpy().any() for m in o3)
+    assert all(inf["iters"] == 0 for row in i3 for inf in row)
+
+
+def test_bad_arguments():
+    require_cuda()
+    p = synth.custom(6, 6, 4, 8, 2, bend=0.1, seed=40)
+    h = pdst.build_G_problem(p, dtypes=("f32",))
+    import torch
+    d = torch.zeros((h.m, 17), dtype=torch.float64, device="cuda")
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_ARG"):
+        pdst.lsqr_batched([h], [d], [1.0], [[0.1] * 17], 10, 1e-6, dtype="f32")
+    d = torch.zeros((h.m, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
+        pdst.lsqr_batched([h], [d], [1.0], [[0.1, 0.2]], 10, 1e-6, dtype="f64")
