@@ -267,6 +267,64 @@ pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, const int32
                               int32_t dtype, double *const *m_out_dev, pdst_lsqr_info *infos,
                               pdst_batched_opts *opts, void *stream);
 
+/*
+ * Column norms c_j = ||[G; w L; lambda I]_{:,j}||_2 of the augmented operator
+ * (c_dev: n FP64, device).  Asynchronous on `stream`.
+ */
+pdst_status pdst_col_norms(pdst_handle_t h, double w, double lambda, double *c_dev, void *stream);
+
+/* Set the handle's right scaling to D_j = c_j^(-p) (p = 1: column-norm
+ * scaling; p = 0: no scaling).  Synchronous. */
+pdst_status pdst_set_col_scaling_power(pdst_handle_t h, double w, double lambda, double p,
+                                       void *stream);
+
+/* ---- learned right-diagonal preconditioner --------------------------------
+ * A small MLP maps 8 per-column features of G to the scaling D of
+ * pdst_set_col_scaling: xh = (f - mu) / sigma, h1 = tanh(W1 xh + b1),
+ * h2 = tanh(W2 h1 + b2), z = w3 . h2 + b3, D = softplus(z).  Parameters are
+ * one FP32 device vector in the order mu[8], sigma[8], W1[64][8], b1[64],
+ * W2[64][64], b2[64], w3[64], b3 (PDST_MLP_NPARAM floats); the last
+ * PDST_MLP_NTRAIN of them (from W1) are trained. */
+#define PDST_MLP_NFEAT 8
+#define PDST_MLP_HIDDEN 64
+#define PDST_MLP_NPARAM (2 * PDST_MLP_NFEAT + PDST_MLP_HIDDEN * PDST_MLP_NFEAT + \
+                         PDST_MLP_HIDDEN + PDST_MLP_HIDDEN * PDST_MLP_HIDDEN + \
+                         2 * PDST_MLP_HIDDEN + 1)
+#define PDST_MLP_NTRAIN (PDST_MLP_NPARAM - 2 * PDST_MLP_NFEAT)
+
+/*
+ * Per-column features of G (feat_dev: n x 8 FP32, device, row = column j):
+ *  f0 log(||G_:j|| + 1e-8)        f1 log(1 + number of rows in column j)
+ *  f2 (k + 1/2) / nz (depth)       f3 sum_r G_rj^2 log T(r) / sum_r G_rj^2 (0 if empty)
+ *  f4, f5, f6 log of the mean, min, max of (||G_:i|| + 1e-8) over the 7-point
+ *             neighbours i of j    f7 log(max_r |G_rj| + 1e-8)
+ * log_periods_host: n_periods values log T (host), T in the units of the
+ * depth-kernel table.  Uses the FP64 values when kept.  Synchronous.
+ */
+pdst_status pdst_precond_features(pdst_handle_t h, const double *log_periods_host, float *feat_dev,
+                                  void *stream);
+
+/* D = softplus(MLP(features)) for n columns: D_dev (FP64) and/or logD_dev
+ * (FP32, log D) may be NULL.  Asynchronous. */
+pdst_status pdst_mlp_forward(const float *params_dev, const float *feat_dev, int64_t n,
+                             double *D_dev, float *logD_dev, void *stream);
+
+/*
+ * Gradient of the mean loss (1/B) sum_s (log D(f_idx[s]) - t[idx[s]])^2 over a
+ * batch of B = batch samples (idx_dev: B int32 row indices into feat_dev and
+ * target_dev).  grad_dev: PDST_MLP_NTRAIN + 1 FP32; the last entry receives
+ * the mean loss.  Per-sample work in one kernel, then a fixed-order sum over
+ * the batch per parameter (deterministic).  Synchronous.
+ */
+pdst_status pdst_mlp_grad(const float *params_dev, const float *feat_dev, const int32_t *idx_dev,
+                          const float *target_dev, int32_t batch, float *grad_dev, void *stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the trained parameters;
+ * m_dev, v_dev: PDST_MLP_NTRAIN FP32 moment vectors.  Asynchronous. */
+pdst_status pdst_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+                          int64_t step, double lr, double beta1, double beta2, double eps,
+                          void *stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdst_last_error_string(void);
 

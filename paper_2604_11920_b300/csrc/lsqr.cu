@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(LT) k_spmv(OpArgs<VT, double> a, int trans,
 // ||[G; w L; lam I]_{:,j}||^2 -> D_j = 1/sqrt(.)  (column-norm scaling).
 template <class VT>
 __global__ void __launch_bounds__(LT) k_colnorm_scale(OpArgs<VT, double> a, double w, double lam,
-                                                      double *D) {
+                                                      double *D, int mode, double pw) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -648,7 +648,10 @@ __global__ void __launch_bounds__(LT) k_colnorm_scale(OpArgs<VT, double> a, doub
             const int deg = (k > 0) + (k < a.nz - 1) + (ix > 0) + (ix < a.nx - 1) + (iy > 0) +
                             (iy < a.ny - 1);
             const double c = s + w * w * ((double)deg * deg + deg) + lam * lam;
-            D[j] = c > 0.0 ? 1.0 / sqrt(c) : 1.0;
+            // mode 0: 1/||A_:j||; 1: ||A_:j||^(-pw); 2: ||A_:j||
+            if (mode == 0) D[j] = c > 0.0 ? 1.0 / sqrt(c) : 1.0;
+            else if (mode == 1) D[j] = c > 0.0 ? pow(c, -0.5 * pw) : 1.0;
+            else D[j] = sqrt(c);
         }
     }
 }
@@ -1007,20 +1010,20 @@ pdst_status spmv_f64(pdst_handle *h, int dtype, int trans, const double *x, doub
 }
 
 static pdst_status colnorm_scaling(pdst_handle *h, double w, double lam, double *D,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int mode = 0, double pw = 1.0) {
     if (h->n == 0) return PDST_OK;
     if (h->vals[PDST_F64].present) {
         auto a = make_args<double, double>(h, PDST_F64, nullptr, false, false);
         unsigned g = persistent_grid(k_colnorm_scale<double>, h->device, (int64_t)h->n * 32);
-        k_colnorm_scale<double><<<g, LT, 0, s>>>(a, w, lam, D);
+        k_colnorm_scale<double><<<g, LT, 0, s>>>(a, w, lam, D, mode, pw);
     } else if (h->vals[PDST_F32].present) {
         auto a = make_args<float, double>(h, PDST_F32, nullptr, false, false);
         unsigned g = persistent_grid(k_colnorm_scale<float>, h->device, (int64_t)h->n * 32);
-        k_colnorm_scale<float><<<g, LT, 0, s>>>(a, w, lam, D);
+        k_colnorm_scale<float><<<g, LT, 0, s>>>(a, w, lam, D, mode, pw);
     } else {
         auto a = make_args<__nv_bfloat16, double>(h, PDST_BF16, nullptr, false, false);
         unsigned g = persistent_grid(k_colnorm_scale<__nv_bfloat16>, h->device, (int64_t)h->n * 32);
-        k_colnorm_scale<__nv_bfloat16><<<g, LT, 0, s>>>(a, w, lam, D);
+        k_colnorm_scale<__nv_bfloat16><<<g, LT, 0, s>>>(a, w, lam, D, mode, pw);
     }
     PDST_CUDA(cudaGetLastError());
     return PDST_OK;
@@ -1097,6 +1100,28 @@ extern "C" pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev
     } else {
         PDST_TRY(colnorm_scaling(h, w, lambda, h->colscale.as<double>(), s));
     }
+    PDST_CUDA(cudaStreamSynchronize(s));
+    h->has_colscale = true;
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_col_norms(pdst_handle_t h, double w, double lambda, double *c_dev,
+                                      void *stream) {
+    PDST_CHECK_ARG(h != nullptr && c_dev != nullptr, "pdst_col_norms: NULL argument");
+    PDST_CHECK_ARG(std::isfinite(w) && std::isfinite(lambda) && w >= 0 && lambda >= 0,
+                   "pdst_col_norms: w and lambda must be finite and >= 0");
+    return colnorm_scaling(h, w, lambda, c_dev, (cudaStream_t)stream, 2, 0.0);
+}
+
+extern "C" pdst_status pdst_set_col_scaling_power(pdst_handle_t h, double w, double lambda,
+                                                  double p, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_set_col_scaling_power: handle is NULL");
+    PDST_CHECK_ARG(std::isfinite(w) && std::isfinite(lambda) && w >= 0 && lambda >= 0,
+                   "pdst_set_col_scaling_power: w and lambda must be finite and >= 0");
+    PDST_CHECK_ARG(std::isfinite(p), "pdst_set_col_scaling_power: p must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    PDST_TRY(h->colscale.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+    PDST_TRY(colnorm_scaling(h, w, lambda, h->colscale.as<double>(), s, 1, p));
     PDST_CUDA(cudaStreamSynchronize(s));
     h->has_colscale = true;
     return PDST_OK;

@@ -92,6 +92,12 @@ SIGNATURES = {
     "pdst_lsqr_noalloc": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
                                  ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_set_col_scaling": (_i32, [_vp, _vp, _d, _d, _vp]),
+    "pdst_col_norms": (_i32, [_vp, _d, _d, _vp, _vp]),
+    "pdst_set_col_scaling_power": (_i32, [_vp, _d, _d, _d, _vp]),
+    "pdst_precond_features": (_i32, [_vp, _vp, _vp, _vp]),
+    "pdst_mlp_forward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "pdst_mlp_grad": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "pdst_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _i64, _d, _d, _d, _d, _vp]),
     "pdst_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
     "pdst_lsqr_batched": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _i32, _d, _i32, _vp,
                                  ctypes.POINTER(LsqrInfo), ctypes.POINTER(BatchedOpts), _vp]),
@@ -255,6 +261,23 @@ class Handle:
                                      _stream(stream)))
         return Result(m_out, info.as_dict())
 
+    def col_norms(self, w, lam, stream=None):
+        import torch
+        c = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(load().pdst_col_norms(self.ptr, w, lam, _dev_ptr(c, self.n), _stream(stream)))
+        return c
+
+    def set_col_scaling_power(self, w, lam, p, stream=None):
+        _check(load().pdst_set_col_scaling_power(self.ptr, w, lam, float(p), _stream(stream)))
+
+    def features(self, log_periods, stream=None):
+        """pdst_precond_features: (n, 8) float32 CUDA tensor."""
+        import torch
+        lp = np.ascontiguousarray(log_periods, dtype=np.float64)
+        f = torch.empty((self.n, MLP_NFEAT), dtype=torch.float32, device="cuda")
+        _check(load().pdst_precond_features(self.ptr, _np_ptr(lp), _dev_ptr(f), _stream(stream)))
+        return f
+
     def set_col_scaling(self, D=None, w=0.0, lam=0.0, stream=None):
         import torch
         p = ctypes.c_void_p(None) if D is None else _dev_ptr(D, self.n, torch.float64, "D")
@@ -316,3 +339,44 @@ def lsqr_batched(handles, ds, w, lams, itmax, tol, dtype="f32", tile_rows=0, kbl
     return m_outs, out_infos, {"chosen_tile_rows": o.chosen_tile_rows,
                                "kernel_launches": o.kernel_launches,
                                "tune_ms": list(o.tune_ms)}
+
+
+MLP_NFEAT, MLP_HIDDEN = 8, 64
+MLP_NPARAM = 2 * 8 + 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+MLP_NTRAIN = MLP_NPARAM - 16
+
+
+def mlp_forward(params, feat, want_D=True, want_logD=False, stream=None):
+    """pdst_mlp_forward: returns (D float64, logD float32) CUDA tensors (or None)."""
+    import torch
+    n = feat.shape[0]
+    D = torch.empty(n, dtype=torch.float64, device="cuda") if want_D else None
+    L = torch.empty(n, dtype=torch.float32, device="cuda") if want_logD else None
+    _check(load().pdst_mlp_forward(_dev_ptr(params, MLP_NPARAM, torch.float32, "params"),
+                                   _dev_ptr(feat, n * MLP_NFEAT, torch.float32, "feat"), n,
+                                   None if D is None else _dev_ptr(D),
+                                   None if L is None else _dev_ptr(L), _stream(stream)))
+    return D, L
+
+
+def mlp_grad(params, feat, idx, target, grad=None, stream=None):
+    """pdst_mlp_grad: gradient of the mean loss over the batch idx; returns the
+    (NTRAIN + 1) float32 tensor whose last entry is the loss."""
+    import torch
+    if grad is None:
+        grad = torch.empty(MLP_NTRAIN + 1, dtype=torch.float32, device="cuda")
+    _check(load().pdst_mlp_grad(_dev_ptr(params, MLP_NPARAM, torch.float32, "params"),
+                                _dev_ptr(feat, None, torch.float32, "feat"),
+                                _dev_ptr(idx, None, torch.int32, "idx"),
+                                _dev_ptr(target, None, torch.float32, "target"),
+                                int(idx.numel()), _dev_ptr(grad, MLP_NTRAIN + 1), _stream(stream)))
+    return grad
+
+
+def mlp_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    import torch
+    _check(load().pdst_mlp_adam(_dev_ptr(params, MLP_NPARAM, torch.float32, "params"),
+                                _dev_ptr(grad, None, torch.float32, "grad"),
+                                _dev_ptr(m, MLP_NTRAIN, torch.float32, "m"),
+                                _dev_ptr(v, MLP_NTRAIN, torch.float32, "v"), int(step),
+                                lr, beta1, beta2, eps, _stream(stream)))
