@@ -1,0 +1,170 @@
+"""Train the learned right-diagonal preconditioner on the GPU.
+
+For each training system (64 x 64 x 16 generator, seeds 10000...):
+  1. build G on the device, compute the 8 column features and the augmented
+     column norms c_j (library kernels);
+  2. search the column-norm power p in {0, 0.25, ..., 1.5}: solve with
+     D = c^-p (FP32 values, FP64 scalars, tol 1e-6) and keep the p with the
+     fewest LSQR iterations (p*);
+  3. target log D_j = -p* log c_j.
+Then fit the MLP (8 -> 64 -> 64 -> 1, softplus output) to the targets by
+mini-batch Adam using the library's gradient and Adam kernels, and write the
+parameters (with the search results) to a JSON file.
+
+Usage:  python -m paper_2604_11920_b300.train_precond --systems 200 \\
+            --out paper_2604_11920_b300/precond_mlp.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import pdst, synth
+
+P_GRID = (1.0, 0.75, 1.25, 0.5, 1.5, 0.25, 0.0)   # search order (likely best first)
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_OUT = os.path.join(HERE, "precond_mlp.json")
+
+
+def make_rhs(h, p):
+    """d = G m_true + noise_frac * RMS(G m_true) * z on the device."""
+    import torch
+    gm = torch.empty(h.m, dtype=torch.float64, device="cuda")
+    h.apply_G(torch.from_numpy(p.m_true).cuda(), gm, dtype="f32")
+    rms = torch.sqrt(torch.mean(gm * gm))
+    return gm + p.noise_frac * rms * torch.from_numpy(p.noise).cuda()
+
+
+def search_power(h, p, d, itmax=5000):
+    """Iterations to tol for each power (solves stop once they exceed the best)."""
+    best, res = None, {}
+    for pw in P_GRID:
+        h.set_col_scaling_power(p.w, p.lam, pw)
+        cap = itmax if best is None else min(itmax, best + 1)
+        r = h.lsqr(d, p.w, p.lam, cap, p.tol, dtype="f32", fmt="blocked", precond=1)
+        it = r.info["iters"] if r.info["istop"] in (1, 2) else cap + 1
+        res[pw] = it
+        if best is None or it < best:
+            best = it
+    pstar = min(res, key=lambda k: (res[k], abs(k - 1.0)))
+    return pstar, res
+
+
+def xavier(rng, fan_out, fan_in):
+    a = math.sqrt(6.0 / (fan_in + fan_out))
+    return rng.uniform(-a, a, size=(fan_out, fan_in))
+
+
+def init_params(rng, mu, sigma):
+    nf, nh = pdst.MLP_NFEAT, pdst.MLP_HIDDEN
+    parts = [mu, sigma, xavier(rng, nh, nf).ravel(), np.zeros(nh), xavier(rng, nh, nh).ravel(),
+             np.zeros(nh), xavier(rng, 1, nh).ravel(), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def collect(seeds, size="mid", log=print):
+    """Features, targets and search results for the given seeds."""
+    import torch
+    feats, targets, table = [], [], []
+    gen = {"mid": synth.mid, "large": synth.large}[size]
+    for i, seed in enumerate(seeds):
+        t0 = time.perf_counter()
+        p = gen(seed)
+        h = pdst.build_G_problem(p, dtypes=("f32",), formats=("blocked",))
+        d = make_rhs(h, p)
+        f = h.features(np.log(p.periods_s))
+        c = h.col_norms(p.w, p.lam)
+        pstar, res = search_power(h, p, d)
+        feats.append(f)
+        targets.append((-pstar * torch.log(c)).to(torch.float32))
+        table.append({"seed": seed, "pstar": pstar, "iters": {str(k): v for k, v in res.items()}})
+        log(f"[{i + 1}/{len(seeds)}] seed {seed}: p* = {pstar}  iters {res}  "
+            f"({time.perf_counter() - t0:.1f} s)")
+        h.close()
+    return torch.cat(feats), torch.cat(targets), table
+
+
+def train(F, T, steps=3000, batch=8192, lr=2e-3, seed=0, log=print):
+    import torch
+    rng = np.random.default_rng(seed)
+    sample = F[torch.randperm(F.shape[0], device="cuda")[:200000]].cpu().numpy().astype(np.float64)
+    mu = sample.mean(axis=0)
+    sd = sample.std(axis=0)
+    sd[sd < 1e-6] = 1.0
+    params = torch.from_numpy(init_params(rng, mu, sd)).cuda()
+    m = torch.zeros(pdst.MLP_NTRAIN, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    grad = torch.empty(pdst.MLP_NTRAIN + 1, dtype=torch.float32, device="cuda")
+    n = F.shape[0]
+    curve = []
+    for step in range(1, steps + 1):
+        idx = torch.from_numpy(rng.integers(0, n, batch).astype(np.int32)).cuda()
+        pdst.mlp_grad(params, F, idx, T, grad)
+        rate = lr * (0.1 ** (step / steps))          # exponential decay to lr / 10
+        pdst.mlp_adam(params, grad, m, v, step, lr=rate)
+        if step % 100 == 0 or step == 1:
+            loss = float(grad[-1].item())
+            curve.append((step, loss))
+            if step % 500 == 0 or step == 1:
+                log(f"step {step}: batch loss {loss:.4e}")
+    # full-data loss
+    _, L = pdst.mlp_forward(params, F, want_D=False, want_logD=True)
+    full = float(torch.mean((L - T) ** 2).item())
+    return params, curve, full
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--systems", type=int, default=200)
+    ap.add_argument("--first-seed", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    F, T, table = collect(range(args.first_seed, args.first_seed + args.systems))
+    t_collect = time.perf_counter() - t0
+    params, curve, full = train(F, T, args.steps, args.batch, args.lr)
+    out = {"model": "MLP 8-64-64-1, tanh hidden, softplus output; D = softplus(z)",
+           "params": [float(x) for x in params.cpu().numpy()],
+           "n_param": pdst.MLP_NPARAM,
+           "train_seeds": [args.first_seed, args.first_seed + args.systems - 1],
+           "generator": "64x64x16 system (synth.mid)",
+           "p_grid": sorted(P_GRID), "search": table,
+           "pstar_histogram": {str(k): sum(1 for r in table if r["pstar"] == k)
+                               for k in sorted(P_GRID)},
+           "train": {"steps": args.steps, "batch": args.batch, "lr": args.lr,
+                     "samples": int(F.shape[0]), "loss_curve": curve, "final_full_loss": full},
+           "seconds": {"collect": t_collect, "total": time.perf_counter() - t0}}
+    with open(args.out, "w") as fh:
+        json.dump(out, fh)
+    print(json.dumps({k: out[k] for k in ("pstar_histogram", "seconds")}),
+          "final loss", full)
+
+
+def load_params(path: str = DEFAULT_OUT):
+    """Trained parameter vector (float32 CUDA tensor) from the JSON file."""
+    import torch
+    with open(path) as fh:
+        rec = json.load(fh)
+    return torch.tensor(rec["params"], dtype=torch.float32, device="cuda")
+
+
+def learned_scaling(h, p, params):
+    """Set the handle's scaling to the network's D for generator problem p."""
+    f = h.features(np.log(p.periods_s))
+    D, _ = pdst.mlp_forward(params, f)
+    h.set_col_scaling(D)
+    return D
+
+
+if __name__ == "__main__":
+    main()
