@@ -38,16 +38,20 @@ sys.path.insert(0, ROOT)
 METRIC = "LSQR time-to-tol (s) & SpMV/SpMV^T HBM GB/s vs plain FP64 GPU LSQR, 1xB300"
 
 FORMS = {
-    # name: (dtype, format, precond)
+    # name: (dtype, format, precond); precond 1 = column-norm, 2 = learned scaling
     "f64-element": ("f64", "element", 0),
     "f64-blocked": ("f64", "blocked", 0),
     "f32-element": ("f32", "element", 0),
     "f32-blocked": ("f32", "blocked", 0),
     "f32-blocked-colnorm": ("f32", "blocked", 1),
     "bf16-blocked-colnorm": ("bf16", "blocked", 1),
+    "f32-blocked-learned": ("f32", "blocked", 2),
 }
 PLAIN = "f64-element"
-DEFAULT_FORM = "f32-blocked-colnorm"
+MODEL_PATH = os.path.join(ROOT, "paper_2604_11920_b300", "precond_mlp.json")
+DEFAULT_FORM = "f32-blocked-learned" if os.path.exists(MODEL_PATH) else "f32-blocked-colnorm"
+ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
+TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9)
 VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
 VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4}
 
@@ -64,6 +68,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-workload section (64 systems x 16 right-hand sides)")
+    ap.add_argument("--batched-systems", type=int, default=64)
     ap.add_argument("--only-solve", action="store_true",
                     help="time the chosen form only (for profiler runs)")
     ap.add_argument("--ncu-case", action="store_true",
@@ -203,9 +210,10 @@ def run_ncu_case(args):
     dtype, fmt, precond = FORMS[args.form]
     h = pdst.build_G_problem(p, dtypes=(dtype,), formats=(fmt,))
     d = torch.from_numpy(p.noise).cuda()
-    if precond:
+    if precond:   # learned and column-norm scaling run the same kernels
         h.set_col_scaling(None, p.w, p.lam)
-    r = h.lsqr(d, p.w, p.lam, 3, 0.0, dtype=dtype, fmt=fmt, precond=precond, use_graph=False)
+    r = h.lsqr(d, p.w, p.lam, 3, 0.0, dtype=dtype, fmt=fmt, precond=1 if precond else 0,
+               use_graph=False)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.form, "iters": r.info["iters"], "nnz": h.nnz}))
     h.close()
@@ -241,12 +249,21 @@ def run_pdst(args, rank, world):
     rms = torch.sqrt(torch.mean(gm * gm))
     d = gm + p.noise_frac * rms * torch.from_numpy(p.noise).cuda()
     itmax = p.itmax
-    if precond:
-        h.set_col_scaling(None, p.w, p.lam)
+    params = None
+    if precond == 2:
+        from paper_2604_11920_b300.train_precond import learned_scaling, load_params
+        params = load_params(MODEL_PATH)
+
+    def set_scaling(pc):
+        if pc == 1:
+            h.set_col_scaling_power(p.w, p.lam, 1.0)
+        elif pc == 2:
+            learned_scaling(h, p, params)     # features + MLP, inside the step
 
     def solve(form, tol=p.tol, **kw):
         dt, fm, pc = FORMS[form]
-        return h.lsqr(d, p.w, p.lam, itmax, tol, dtype=dt, fmt=fm, precond=pc, **kw)
+        set_scaling(pc)
+        return h.lsqr(d, p.w, p.lam, itmax, tol, dtype=dt, fmt=fm, precond=1 if pc else 0, **kw)
 
     def timed(form, steps, warmup):
         for _ in range(warmup):
@@ -297,12 +314,35 @@ def run_pdst(args, rank, world):
     def relerr(a):
         return float(torch.linalg.norm(a - ref.m) / torch.linalg.norm(ref.m))
 
+    # time to reach the FP64 reference within ACC_TARGET: loosest tolerance of
+    # the ladder whose solution is that close, per form
+    def to_accuracy(form):
+        for tol in TOL_LADDER:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = solve(form, tol=tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            err = relerr(r.m)
+            if err <= ACC_TARGET:
+                return {"tol": tol, "s": e0.elapsed_time(e1) / 1e3, "iters": r.info["iters"],
+                        "model_error": err}
+        return {"tol": None, "s": None, "iters": None, "model_error": err}
+
+    acc_chosen = to_accuracy(args.form)
+    acc_plain = to_accuracy(PLAIN)
+    accuracy_matched = {"target_model_error": ACC_TARGET, "chosen": acc_chosen,
+                        "plain_fp64": acc_plain,
+                        "speedup": (acc_plain["s"] / acc_chosen["s"])
+                        if acc_plain["s"] and acc_chosen["s"] else None}
+
     # per-kernel device time (events around each launch, same solve)
     prof = solve(args.form, profile=True)
     pi = max(prof.info["profiled_iters"], 1)
     kms = {"fwd": prof.info["fwd_ms"] / pi, "adj": prof.info["adj_ms"] / pi,
            "upd": prof.info["upd_ms"] / pi}
-    ab = algorithmic_bytes(h, p, dtype, fmt, bool(precond))
+    ab = algorithmic_bytes(h, p, dtype, fmt, precond > 0)
     dom = max(("fwd", "adj"), key=lambda k: kms[k])
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
@@ -326,12 +366,15 @@ def run_pdst(args, rank, world):
         mh = torch.empty(h.n, dtype=torch.float64, pin_memory=True)
         dn, mn = dh.numpy(), mh.numpy()
         dt_, fm_, pc_ = FORMS[args.form]
-        h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=pc_)
+        set_scaling(pc_)
+        h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=min(pc_, 1))
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=pc_)
+            set_scaling(pc_)
+            h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_,
+                        precond=min(pc_, 1))
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         if world > 1:
@@ -357,17 +400,86 @@ def run_pdst(args, rank, world):
         "plain_fp64": {"s": ms_plain / 1e3, "iters": res_plain.info["iters"],
                        "model_error_vs_fp64_ref": relerr(m_plain)},
         "speedup_vs_plain_fp64": ms_plain / ms,
+        "accuracy_matched": accuracy_matched,
         "kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
         "spmv_gbs": spmv_gbs,
         "build_G_s": build_s,
         "iters_per_s": it_chosen / (ms / 1e3),
     })
 
+    h.close()
+    if not args.no_batched:
+        out["batched"] = batched_section(args.batched_systems)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_sample_iters, res_plain.info["iters"])
-    h.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def batched_section(nsys=64, steps=2):
+    """The batched workload: nsys uneven systems (grids 24x24x8 .. 64x64x16),
+    16 right-hand sides each sharing G (8 checkerboards at the system's
+    lambda, the blob model at 8 damping values 1e-3..1), FP32 values, tol 1e-6,
+    solved by pdst_lsqr_batched.  Compared with one-at-a-time FP32 solves of the
+    same pairs on a sample of systems, scaled by stored entries x pairs."""
+    import numpy as np
+    import torch
+
+    from paper_2604_11920_b300 import pdst, synth
+    ps = synth.batched(nsys)
+    hs, ds, lams = [], [], []
+    for p in ps:
+        h = pdst.build_G_problem(p, dtypes=("f32",), formats=("blocked",))
+        cols = []
+        for j, (model, lam) in enumerate(synth.batched_rhs_models(p)):
+            gm = torch.empty(h.m, dtype=torch.float64, device="cuda")
+            h.apply_G(torch.from_numpy(model).cuda(), gm, dtype="f32")
+            rms = torch.sqrt(torch.mean(gm * gm))
+            z = torch.from_numpy(synth.rhs_noise(p.seed, p.m_rows, j)).cuda()
+            cols.append(gm + p.noise_frac * rms * z)
+        ds.append(torch.stack(cols, dim=1).contiguous())
+        lams.append([lam for _, lam in synth.batched_rhs_models(p)])
+        hs.append(h)
+    w = [p.w for p in ps]
+    nnz = [h.nnz for h in hs]
+    outs, infos, opts = pdst.lsqr_batched(hs, ds, w, lams, 2000, 1e-6, dtype="f32")  # + tune
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        outs, infos, opts2 = pdst.lsqr_batched(hs, ds, w, lams, 2000, 1e-6, dtype="f32")
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / steps
+    iters = [inf["iters"] for row in infos for inf in row]
+    conv = sum(inf["istop"] in (1, 2) for row in infos for inf in row)
+    # one-at-a-time reference on a sample of systems (largest, median, smallest)
+    order = np.argsort(nnz)
+    sample = sorted({int(order[-1]), int(order[len(order) // 2]), int(order[0])})
+    t_single, work_single = 0.0, 0
+    for s in sample:
+        for j in range(ds[s].shape[1]):
+            dj = ds[s][:, j].contiguous()
+            hs[s].lsqr(dj, w[s], lams[s][j], 2000, 1e-6, dtype="f32", fmt="blocked")
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            hs[s].lsqr(dj, w[s], lams[s][j], 2000, 1e-6, dtype="f32", fmt="blocked")
+            torch.cuda.synchronize()
+            t_single += time.perf_counter() - t1
+        work_single += nnz[s] * ds[s].shape[1]
+    total_work = sum(n * d.shape[1] for n, d in zip(nnz, ds))
+    t_seq_est = t_single * total_work / work_single
+    for h in hs:
+        h.close()
+    return {"workload": f"{nsys} systems (grids 24x24x8..64x64x16), 16 right-hand sides each, "
+                        "FP32 values, tol 1e-6",
+            "total_nnz": int(sum(nnz)), "pairs": len(iters), "converged_pairs": conv,
+            "batch_s": t_batch, "solves_per_s": len(iters) / t_batch,
+            "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
+            "chosen_tile_rows": opts["chosen_tile_rows"], "autotune_fwd_ms": opts["tune_ms"][:3],
+            "gpu_launches": opts2["kernel_launches"],
+            "one_at_a_time_estimate_s": t_seq_est,
+            "speedup_vs_one_at_a_time": t_seq_est / t_batch,
+            "one_at_a_time_sample": f"systems {sample} ({sum(ds[s].shape[1] for s in sample)} "
+                                    "single solves), scaled by stored entries x right-hand sides"}
 
 
 def cpu_baseline(p, sample_iters, iters_to_tol):
