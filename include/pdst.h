@@ -205,9 +205,10 @@ pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lam
  * overlap on the GPU -- from two host threads or on two streams -- race and
  * give wrong results.  Synchronous on `stream`.
  * Errors: as pdst_lsqr, plus PDST_ERR_LIMIT when the system's scratch exceeds
- * 16 MiB: 8 (m + 3n) + 16 n bytes in FP64, 4 (m + 3n) + 16 n in FP32/BF16,
- * plus about 100 KiB, plus n more vector entries when lambda rows are appended
- * (e.g. the 64 x 64 x 16 system with 171,360 rows needs about 4.5 MB).
+ * 16 MiB: s (m + 3n) + 16 n bytes (s = 8 in FP64, 4 in FP32/BF16), plus
+ * s (nnz / 256 + n) for the adjoint's per-chunk sums, plus about 100 KiB,
+ * plus n more vector entries when lambda rows are appended (e.g. the
+ * 64 x 64 x 16 system with 171,360 rows needs about 8.5 MB in FP64).
  */
 pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, double w, double lambda,
                               int32_t itmax, double tol, double *m_out_dev,

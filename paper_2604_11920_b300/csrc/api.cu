@@ -141,6 +141,24 @@ extern "C" pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t
                             rows[rptr[c] + q];
         }
     }
-    if (val_host) PDST_TRY(values_to_host(dtype, h->vals[dtype].csc.p, h->nnz, val_host));
+    if (val_host) {
+        if (elem) {
+            PDST_TRY(values_to_host(dtype, h->vals[dtype].csc.p, h->nnz, val_host));
+        } else {
+            // reorder the blocked CSC values (cell, row, depth) to column order
+            std::vector<double> b(h->nnz);
+            PDST_TRY(values_to_host(dtype, h->vals[dtype].bcsc.p, h->nnz, b.data()));
+            std::vector<int64_t> rptr;
+            std::vector<int32_t> cnt;
+            PDST_TRY(d2h(rptr, h->cell_rptr, (int64_t)h->H + 1));
+            PDST_TRY(d2h(cnt, h->cell_cnt, h->H));
+            const int nz = h->nz;
+            for (int32_t c = 0; c < h->H; ++c)
+                for (int q = 0; q < cnt[c]; ++q)
+                    for (int k = 0; k < nz; ++k)
+                        val_host[(int64_t)nz * rptr[c] + (int64_t)k * cnt[c] + q] =
+                            b[(rptr[c] + q) * nz + k];
+        }
+    }
     return PDST_OK;
 }

@@ -43,7 +43,7 @@ template <class VT, class ST> struct BSys {
     const int32_t *cell_cnt;
     const int32_t *cell_rows;
     const int32_t *cell_order;
-    const VT *valT;
+    const VT *valB;   // blocked CSC values
     ST *U;            // (m + n) x R, right-hand side fastest
     ST *V;            // n x R
     double *X, *W;    // n x R
@@ -231,15 +231,22 @@ __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const 
             const int nk = nz - k0 < 4 ? nz - k0 : 4;
             const int64_t c0 = __ldg(S.cell_rptr + h);
             const int cnt = __ldg(S.cell_cnt + h);
-            const VT *vb = S.valT + (int64_t)nz * c0 + (int64_t)k0 * cnt;
+            const VT *vb = S.valB + c0 * nz + k0;
             const int32_t *rows = S.cell_rows + c0;
             AT acc[4] = {0, 0, 0, 0};
             for (int q = half; q < cnt; q += 2) {
                 const int r = __ldg(rows + q);
                 const AT ur = (AT)S.U[(int64_t)r * R + jj];
+                if (nk == 4 && (nz & 3) == 0) {
+                    typename Wide<VT>::T w4[4];
+                    Pack4<VT>::ld(vb + (int64_t)q * nz, w4);
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (t < nk) acc[t] += (AT)ldval(vb + (int64_t)t * cnt + q) * ur;
+                    for (int t = 0; t < 4; ++t) acc[t] += (AT)w4[t] * ur;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (t < nk) acc[t] += (AT)widen(vb[(int64_t)q * nz + t]) * ur;
+                }
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], 16);
@@ -478,7 +485,7 @@ template <class VT, class ST> struct Batched {
             q.cell_cnt = h->cell_cnt.as<int32_t>();
             q.cell_rows = h->cell_rows.as<int32_t>();
             q.cell_order = h->cell_order.as<int32_t>();
-            q.valT = h->vals[dtype].csc.as<VT>();
+            q.valB = h->vals[dtype].bcsc.as<VT>();
             q.U = bw->bufs[4 * i]->as<ST>();
             q.V = bw->bufs[4 * i + 1]->as<ST>();
             q.X = bw->bufs[4 * i + 2]->as<double>();

@@ -249,6 +249,20 @@ __global__ void k_chunk_place(int64_t m, int ch, int H, const int64_t *__restric
     }
 }
 
+// Blocked CSC copy: the nz values of run e (row r, cell h) go to the run's
+// position in the cell's row list, depth fastest.
+template <class T>
+__global__ void k_bcsc_values(int64_t U, int nz, const int64_t *__restrict__ run_pos,
+                              const T *__restrict__ csr, T *__restrict__ bcsc) {
+    int64_t total = U * nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = i / nz;
+        int k = (int)(i - e * nz);
+        bcsc[run_pos[e] * nz + k] = csr[i];
+    }
+}
+
 template <class T>
 __global__ void k_csc_values(int64_t U, int nz, const int32_t *__restrict__ cells,
                              const int64_t *__restrict__ run_pos,
@@ -479,7 +493,9 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
         if (!(dtypes & (1u << d))) continue;
         size_t es = d == PDST_F64 ? 8 : d == PDST_F32 ? 4 : 2;
         PDST_TRY(h->vals[d].csr.alloc(es * std::max<int64_t>(nnz, 1)));
-        PDST_TRY(h->vals[d].csc.alloc(es * std::max<int64_t>(nnz, 1)));
+        PDST_TRY(h->vals[d].bcsc.alloc(es * std::max<int64_t>(nnz, 1)));
+        if (h->formats & (1u << PDST_FMT_ELEMENT))
+            PDST_TRY(h->vals[d].csc.alloc(es * std::max<int64_t>(nnz, 1)));
         h->vals[d].present = true;
     }
     if (nnz) {
@@ -523,23 +539,38 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
                                                        d_runpos.as<int64_t>());
         PDST_CUDA(cudaGetLastError());
         unsigned g = grid_for(nnz, 256, h->device);
-        if (h->vals[0].present)
-            k_csc_values<double><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(),
-                                                  d_runpos.as<int64_t>(), h->cell_rptr.as<int64_t>(),
-                                                  h->cell_cnt.as<int32_t>(),
-                                                  h->vals[0].csr.as<double>(),
-                                                  h->vals[0].csc.as<double>());
-        if (h->vals[1].present)
-            k_csc_values<float><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(),
-                                                 d_runpos.as<int64_t>(), h->cell_rptr.as<int64_t>(),
-                                                 h->cell_cnt.as<int32_t>(),
-                                                 h->vals[1].csr.as<float>(),
-                                                 h->vals[1].csc.as<float>());
-        if (h->vals[2].present)
-            k_csc_values<__nv_bfloat16><<<g, 256, 0, s>>>(
-                U, nz, h->row_cells.as<int32_t>(), d_runpos.as<int64_t>(),
-                h->cell_rptr.as<int64_t>(), h->cell_cnt.as<int32_t>(),
-                h->vals[2].csr.as<__nv_bfloat16>(), h->vals[2].csc.as<__nv_bfloat16>());
+        const bool elem = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
+        const int64_t *rp = d_runpos.as<int64_t>();
+        if (h->vals[0].present) {
+            k_bcsc_values<double><<<g, 256, 0, s>>>(U, nz, rp, h->vals[0].csr.as<double>(),
+                                                   h->vals[0].bcsc.as<double>());
+            if (elem)
+                k_csc_values<double><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
+                                                      h->cell_rptr.as<int64_t>(),
+                                                      h->cell_cnt.as<int32_t>(),
+                                                      h->vals[0].csr.as<double>(),
+                                                      h->vals[0].csc.as<double>());
+        }
+        if (h->vals[1].present) {
+            k_bcsc_values<float><<<g, 256, 0, s>>>(U, nz, rp, h->vals[1].csr.as<float>(),
+                                                  h->vals[1].bcsc.as<float>());
+            if (elem)
+                k_csc_values<float><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
+                                                     h->cell_rptr.as<int64_t>(),
+                                                     h->cell_cnt.as<int32_t>(),
+                                                     h->vals[1].csr.as<float>(),
+                                                     h->vals[1].csc.as<float>());
+        }
+        if (h->vals[2].present) {
+            k_bcsc_values<__nv_bfloat16><<<g, 256, 0, s>>>(U, nz, rp,
+                                                          h->vals[2].csr.as<__nv_bfloat16>(),
+                                                          h->vals[2].bcsc.as<__nv_bfloat16>());
+            if (elem)
+                k_csc_values<__nv_bfloat16><<<g, 256, 0, s>>>(
+                    U, nz, h->row_cells.as<int32_t>(), rp, h->cell_rptr.as<int64_t>(),
+                    h->cell_cnt.as<int32_t>(), h->vals[2].csr.as<__nv_bfloat16>(),
+                    h->vals[2].csc.as<__nv_bfloat16>());
+        }
         PDST_CUDA(cudaGetLastError());
         PDST_CUDA(cudaStreamSynchronize(s));   // chunk tables are released on scope exit
     }
@@ -577,6 +608,20 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
                          [&](int a, int b) { return cnt[a] > cnt[b]; });
         PDST_TRY(h->cell_order.alloc(sizeof(int32_t) * H));
         PDST_CUDA(cudaMemcpy(h->cell_order.p, order.data(), sizeof(int32_t) * H,
+                             cudaMemcpyHostToDevice));
+        // adjoint work items: every cell (empty ones too) in chunks of
+        // ADJ_CHUNK rows, cells longest first, chunks of a cell consecutive
+        std::vector<int32_t> items;
+        for (int i = 0; i < H; ++i) {
+            const int c = order[i];
+            for (int q0 = 0; q0 < std::max(cnt[c], 1); q0 += ADJ_CHUNK) {
+                items.push_back(c);
+                items.push_back(q0);
+            }
+        }
+        h->n_adj = (int64_t)items.size() / 2;
+        PDST_TRY(h->adj_item.alloc(sizeof(int32_t) * items.size()));
+        PDST_CUDA(cudaMemcpy(h->adj_item.p, items.data(), sizeof(int32_t) * items.size(),
                              cudaMemcpyHostToDevice));
     }
     return PDST_OK;

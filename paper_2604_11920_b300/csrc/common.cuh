@@ -101,9 +101,14 @@ struct LsqrSync {
 
 struct ValueSet {
     DevBuf csr;   // values in CSR order (row-major, cells ascending, depth fastest)
-    DevBuf csc;   // values in CSC order (column-major, rows ascending)
+    DevBuf csc;   // element CSC order: column j = h*nz+k at nz*cell_rptr[h] + k*cnt[h]
+                  // (kept with the element layout only)
+    DevBuf bcsc;  // blocked CSC order: entry (cell h, row q, depth k) at
+                  // (cell_rptr[h] + q)*nz + k, depth fastest (always kept)
     bool present = false;
 };
+
+constexpr int ADJ_CHUNK = 256;   // rows of one cell per adjoint work item
 
 struct LsqrWork;   // lsqr.cu
 
@@ -138,6 +143,8 @@ struct pdst_handle {
     pdst::DevBuf cell_rows;    // int32 [U]    rows of each cell (ascending)
     pdst::DevBuf cell_cnt;     // int32 [H]    rows per cell
     pdst::DevBuf cell_order;   // int32 [H]    cells by descending row count (work order)
+    pdst::DevBuf adj_item;     // int32 [2*n_adj]  (cell, first row) of each adjoint work item
+    int64_t n_adj = 0;         // adjoint work items: chunks of ADJ_CHUNK rows, longest cells first
     // element indices (PDST_FMT_ELEMENT)
     pdst::DevBuf row_ptr;      // int64 [m+1]
     pdst::DevBuf col;          // int32 [nnz]

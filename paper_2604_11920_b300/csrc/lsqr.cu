@@ -47,7 +47,12 @@ template <class VT, class ST> struct OpArgs {
     const int32_t *cell_cnt;
     const int32_t *cell_order;
     const VT *val;            // CSR order
-    const VT *valT;           // CSC order
+    const VT *valT;           // element CSC order (element layout only)
+    const VT *valB;           // blocked CSC order
+    const int32_t *adj_item;  // (cell, first row) per adjoint work item
+    int64_t n_adj;
+    ST *chunk_part;           // n_adj x nz partial column sums (multi-chunk cells)
+    unsigned *cell_done;      // H finished-chunk counters
     const double *D;          // right diagonal scaling or nullptr
     int lam_rows_on;          // append lambda*D rows
     ST *ubar;                 // M = m + n (+ n)
@@ -125,30 +130,23 @@ __device__ __forceinline__ AT dot_blk_row(const int64_t *__restrict__ row_cptr,
     return warp_sum(s);
 }
 
-// Blocked CSC column j = h*nz + k: rows cell_rows[cell_rptr[h] + q] shared by
-// the nz columns of the cell, values valT[nz*cell_rptr[h] + k*cnt[h] + q].
+// Blocked CSC column j = h*nz + k: rows cell_rows[cell_rptr[h] + q], values
+// valB[(cell_rptr[h] + q)*nz + k] (used by pdst_apply_G).
 template <class VT, class AT, class XT>
 __device__ __forceinline__ AT dot_blk_col(const int64_t *__restrict__ cell_rptr,
                                           const int32_t *__restrict__ cell_cnt,
                                           const int32_t *__restrict__ cell_rows,
-                                          const VT *__restrict__ valT, const XT *__restrict__ u,
+                                          const VT *__restrict__ valB, const XT *__restrict__ u,
                                           int64_t j, int nz, int lane) {
     const int64_t h = j / nz;
     const int k = (int)(j - h * nz);
     const int64_t c0 = cell_rptr[h];
     const int cnt = cell_cnt[h];
-    const VT *v = valT + (int64_t)nz * c0 + (int64_t)k * cnt;
+    const VT *v = valB + c0 * nz + k;
     const int32_t *rows = cell_rows + c0;
-    AT s0 = 0, s1 = 0;
-    int q = lane;
-    for (; q + 32 < cnt; q += 64) {
-        AT a0 = (AT)ldval(v + q), a1 = (AT)ldval(v + q + 32);
-        int r0 = __ldg(rows + q), r1 = __ldg(rows + q + 32);
-        s0 += a0 * (AT)__ldg(u + r0);
-        s1 += a1 * (AT)__ldg(u + r1);
-    }
-    if (q < cnt) s0 += (AT)ldval(v + q) * (AT)__ldg(u + __ldg(rows + q));
-    return warp_sum(s0 + s1);
+    AT s = 0;
+    for (int q = lane; q < cnt; q += 32) s += (AT)widen(v[(int64_t)q * nz]) * (AT)__ldg(u + rows[q]);
+    return warp_sum(s);
 }
 
 // ------------------------------------------- blocked products, LSQR sweeps
@@ -331,69 +329,136 @@ __device__ __forceinline__ double adj_finish(const OpArgs<VT, ST> &a, int64_t j,
     return (double)v * (double)v;
 }
 
-// G^T rows of the adjoint sweep in the blocked layout.  Work item = (cell,
-// group of up to four depths), cells in descending length order: the warp
-// reads each row index of the cell once, gathers u once per row and streams
-// the four depth columns' values (contiguous in the CSC value order).
-template <class VT, class ST>
-__device__ __forceinline__ double adj_cols_blk(const OpArgs<VT, ST> &a, ST ib, ST cv, ST wsm,
-                                               ST lamr, int init, int64_t gw, int64_t nw,
-                                               int lane) {
+// G^T rows of the adjoint sweep in the blocked CSC layout.  Work item = a
+// chunk of up to ADJ_CHUNK rows of one cell (cells longest first).  A row's
+// nz values are contiguous, so L = nz / G lanes share a row, each reading G
+// consecutive depths (G = 4: one 16-byte vector) and the row's u once
+// (broadcast); 32 / L rows per step, UN steps of loads in flight, row
+// indices fetched one step ahead.  Per-depth sums are combined across the
+// warp through shared memory in a fixed order; a cell split over several
+// chunks is finished by its last chunk, which adds the chunks' partial sums
+// in chunk order.
+template <class VT, class ST, int G>
+__device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST ib, ST cv, ST wsm,
+                                                    ST lamr, int init, int64_t gw, int64_t nw,
+                                                    int lane) {
     using AT = ST;
     constexpr int UN = Unroll<AT>::U;
+    __shared__ AT red[LT / 32][32][G];
+    __shared__ int last_flag[LT / 32];
+    const int warp = threadIdx.x >> 5;
     const int nz = a.nz;
-    const int kg = (nz + 3) >> 2;
-    const int64_t H = (int64_t)a.nx * a.ny;
-    const int64_t items = H * kg;
+    const int L = nz / G;                  // lanes per row
+    const int rps = 32 / L;                // rows per step
+    const int act = rps * L;
+    const int rl = lane / L, gi = lane - (lane / L) * L;
     double ss = 0.0;
-    for (int64_t it = gw; it < items; it += nw) {
-        const int h = __ldg(a.cell_order + it / kg);
-        const int k0 = 4 * (int)(it % kg);
-        const int nk = nz - k0 < 4 ? nz - k0 : 4;
+    for (int64_t it = gw; it < a.n_adj; it += nw) {
+        const int h = __ldg(a.adj_item + 2 * it);
+        const int q0 = __ldg(a.adj_item + 2 * it + 1);
         const int64_t c0 = __ldg(a.cell_rptr + h);
         const int cnt = __ldg(a.cell_cnt + h);
-        const VT *vb = a.valT + (int64_t)nz * c0 + (int64_t)k0 * cnt;
+        const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
         const int32_t *rows = a.cell_rows + c0;
-        AT acc[4] = {0, 0, 0, 0};
-        // row indices are fetched one chunk ahead of the u gathers that use them
+        const VT *vb = a.valB + c0 * nz + G * gi;
+        AT acc[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) acc[t] = 0;
         int rn[UN];
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
-            const int q = lane + 32 * u;
-            rn[u] = q < cnt ? __ldg(rows + q) : -1;
+            const int q = q0 + rl + rps * u;
+            rn[u] = (lane < act && q < q1) ? __ldg(rows + q) : -1;
         }
-        for (int qb = 0; qb < cnt; qb += 32 * UN) {
+        for (int qb = q0; qb < q1; qb += rps * UN) {
             int rr[UN];
             AT uu[UN];
-            AT vv[UN][4];
+            AT vv[UN][G];
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
                 rr[u] = rn[u];
-                const int q = qb + 32 * UN + lane + 32 * u;
-                rn[u] = q < cnt ? __ldg(rows + q) : -1;
+                const int q = qb + rps * UN + rl + rps * u;
+                rn[u] = (lane < act && q < q1) ? __ldg(rows + q) : -1;
             }
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
-                const int q = qb + lane + 32 * u;
+                const int q = qb + rl + rps * u;
+                if (rr[u] >= 0) {
+                    if (G == 4) {
+                        typename Wide<VT>::T w4[4];
+                        Pack4<VT>::ld(vb + (int64_t)q * nz, w4);
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    vv[u][t] = (q < cnt && t < nk) ? (AT)ldval(vb + (int64_t)t * cnt + q) : (AT)0;
+                        for (int t = 0; t < G; ++t) vv[u][t] = (AT)w4[t];
+                    } else {
+                        vv[u][0] = (AT)ldval(vb + (int64_t)q * nz);
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < G; ++t) vv[u][t] = 0;
+                }
             }
 #pragma unroll
             for (int u = 0; u < UN; ++u) uu[u] = rr[u] >= 0 ? (AT)__ldg(a.ubar + rr[u]) : (AT)0;
 #pragma unroll
             for (int u = 0; u < UN; ++u)
 #pragma unroll
-                for (int t = 0; t < 4; ++t) acc[t] += vv[u][t] * uu[u];
+                for (int t = 0; t < G; ++t) acc[t] += vv[u][t] * uu[u];
         }
+        // per-depth sums over the rows of the step, in a fixed order
 #pragma unroll
-        for (int t = 0; t < 4; ++t) acc[t] = warp_sum(acc[t]);
-        if (lane < nk) {
-            AT mine = acc[0];
-            if (lane == 1) mine = acc[1];
-            if (lane == 2) mine = acc[2];
-            if (lane == 3) mine = acc[3];
-            ss += adj_finish(a, (int64_t)h * nz + k0 + lane, mine, ib, cv, wsm, lamr, init);
+        for (int t = 0; t < G; ++t) red[warp][lane][t] = acc[t];
+        __syncwarp();
+        AT dot[2] = {0, 0};   // depths lane and lane + 32 (nz <= 64)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int k = lane + 32 * half;
+            if (k < nz) {
+                const int g = k / G, t = k - (k / G) * G;
+                AT sum = 0;
+                for (int r = 0; r < rps; ++r) sum += red[warp][g + L * r][t];
+                dot[half] = sum;
+            }
+        }
+        __syncwarp();
+        const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+        bool finish = true;
+        if (nch > 1) {
+            const int64_t first = it - q0 / ADJ_CHUNK;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int k = lane + 32 * half;
+                if (k < nz) a.chunk_part[it * nz + k] = dot[half];
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                const unsigned prev = atomicAdd(a.cell_done + h, 1u);
+                last_flag[warp] = prev == (unsigned)(nch - 1);
+            }
+            __syncwarp();
+            finish = last_flag[warp] != 0;
+            if (finish) {
+                __threadfence();
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int k = lane + 32 * half;
+                    if (k < nz) {
+                        AT sum = 0;
+                        for (int c = 0; c < nch; ++c)
+                            sum += (AT)__ldcg(a.chunk_part + (first + c) * nz + k);
+                        dot[half] = sum;
+                    }
+                }
+                if (lane == 0) a.cell_done[h] = 0u;
+            }
+        }
+        if (finish) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int k = lane + 32 * half;
+                if (k < nz)
+                    ss += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr, init);
+            }
         }
     }
     return ss;
@@ -535,7 +600,9 @@ __global__ void __launch_bounds__(LT, 4) k_adj(OpArgs<VT, ST> a, int init) {
     double ss = 0.0;
     if (!skip) {
         if (FMT == FMT_BLK) {
-            ss = adj_cols_blk<VT, ST>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+            ss = (a.nz & 3) == 0 && a.nz <= 64
+                     ? adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane)
+                     : adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
         } else {
             for (int64_t j = gw; j < a.n; j += nw) {
                 AT dot = dot_elem<VT, AT, ST>(a.col_ptr, a.row_idx, a.valT, a.ubar, j, lane);
@@ -619,7 +686,7 @@ __global__ void __launch_bounds__(LT) k_spmv(OpArgs<VT, double> a, int trans,
             s = FMT == FMT_ELEM
                     ? dot_elem<VT, double, double>(a.col_ptr, a.row_idx, a.valT, xin, r, lane)
                     : dot_blk_col<VT, double, double>(a.cell_rptr, a.cell_cnt, a.cell_rows,
-                                                      a.valT, xin, r, a.nz, lane);
+                                                      a.valB, xin, r, a.nz, lane);
         if (lane == 0) y[r] = s;
     }
 }
@@ -636,10 +703,10 @@ __global__ void __launch_bounds__(LT) k_colnorm_scale(OpArgs<VT, double> a, doub
         const int k = (int)(j - h * a.nz);
         const int64_t c0 = a.cell_rptr[h];
         const int cnt = a.cell_cnt[h];
-        const VT *v = a.valT + (int64_t)a.nz * c0 + (int64_t)k * cnt;
+        const VT *v = a.valB + c0 * a.nz + k;
         double s = 0.0;
         for (int q = lane; q < cnt; q += 32) {
-            double t = (double)widen(v[q]);
+            double t = (double)widen(v[(int64_t)q * a.nz]);
             s += t * t;
         }
         s = warp_sum(s);
@@ -662,7 +729,7 @@ struct LsqrWork {
     int dtype = -1, format = -1, lamrows = -1;
     const void *graph_D = nullptr;
     int64_t M = 0;
-    DevBuf ubar, vbar, vsc, x, wv, partial, scal, sync;
+    DevBuf ubar, vbar, vsc, x, wv, partial, scal, sync, chunk_part, cell_done;
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
     std::map<int, cudaGraphExec_t> graphs;   // key: kblock
@@ -695,6 +762,9 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     a.cell_order = h->cell_order.as<int32_t>();
     a.val = h->vals[dtype].csr.as<VT>();
     a.valT = h->vals[dtype].csc.as<VT>();
+    a.valB = h->vals[dtype].bcsc.as<VT>();
+    a.adj_item = h->adj_item.as<int32_t>();
+    a.n_adj = h->n_adj;
     a.D = scaled ? h->colscale.as<double>() : nullptr;
     a.lam_rows_on = lamrows ? 1 : 0;
     if (w) {
@@ -706,6 +776,8 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
         a.partial = w->partial.as<double>();
         a.sc = w->scal.as<LsqrScalars>();
         a.sy = w->sync.as<LsqrSync>();
+        a.chunk_part = w->chunk_part.as<ST>();
+        a.cell_done = w->cell_done.as<unsigned>();
     }
     return a;
 }
@@ -738,6 +810,8 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_TRY(w->partial.alloc(sizeof(double) * 3 * MAXBLK));
         PDST_TRY(w->scal.alloc(sizeof(LsqrScalars)));
         PDST_TRY(w->sync.alloc(sizeof(LsqrSync)));
+        PDST_TRY(w->chunk_part.alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz, 1)));
+        PDST_TRY(w->cell_done.alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
         if (!w->h_scal) PDST_CUDA(cudaMallocHost(&w->h_scal, sizeof(LsqrScalars)));
         w->M = M;
         // warp-per-row kernels: items = rows * 32 threads
@@ -789,6 +863,7 @@ template <class VT, class ST, int FMT> struct Solver {
                            bool profile, double *m_out, cudaStream_t s, RunStats &rs) {
         OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, scaled, lamrows);
         PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
+        PDST_CUDA(cudaMemsetAsync(w->cell_done.p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
         *w->h_scal = init;
         PDST_CUDA(cudaMemcpyAsync(w->scal.p, w->h_scal, sizeof(LsqrScalars),
                                   cudaMemcpyHostToDevice, s));
@@ -862,6 +937,8 @@ static pdst_status dispatch_run(pdst_handle *h, LsqrWork *w, int dtype, bool sca
                                     profile, m_out, s, rs);
 }
 
+static bool blocked_nz_ok(int nz) { return (nz % 4 == 0) ? nz <= 64 : nz <= 32; }
+
 static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, double lam,
                              int32_t itmax, double tol, double *m_out, pdst_lsqr_info *info,
                              const pdst_lsqr_opts *o, cudaStream_t s) {
@@ -884,6 +961,10 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     if (fmt == PDST_FMT_ELEMENT && !(h->formats & (1u << PDST_FMT_ELEMENT))) {
         set_error("pdst_lsqr: element indices were not built");
         return PDST_ERR_STATE;
+    }
+    if (fmt == PDST_FMT_BLOCKED && !blocked_nz_ok(h->nz)) {
+        set_error("pdst_lsqr: the blocked layout needs nz <= 64 (nz <= 32 unless nz %% 4 == 0)");
+        return PDST_ERR_LIMIT;
     }
     const bool scaled = opts.precond == 1;
     if (scaled && !h->has_colscale) {
@@ -1171,10 +1252,11 @@ static pdst_status noalloc_scratch(int device, unsigned char **out) {
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Bytes of scratch one solve needs, in the carving order used below.
-static size_t noalloc_need(int64_t M, int64_t n, size_t st) {
+static size_t noalloc_need(int64_t M, int64_t n, size_t st, int64_t chunk_vals, int64_t H) {
     return align256(sizeof(LsqrScalars)) + align256(sizeof(LsqrSync)) +
            align256(sizeof(double) * 3 * MAXBLK) + align256(st * M) + 2 * align256(st * n) +
-           2 * align256(sizeof(double) * n);
+           2 * align256(sizeof(double) * n) + align256(st * chunk_vals) +
+           align256(sizeof(unsigned) * H);
 }
 
 template <class VT, class ST, int FMT>
@@ -1197,8 +1279,12 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     auto *vsc = reinterpret_cast<ST *>(carve(sizeof(ST) * h->n));
     auto *x = reinterpret_cast<double *>(carve(sizeof(double) * h->n));
     auto *wv = reinterpret_cast<double *>(carve(sizeof(double) * h->n));
+    auto *cpart = reinterpret_cast<ST *>(carve(sizeof(ST) * h->n_adj * h->nz));
+    auto *cdone = reinterpret_cast<unsigned *>(carve(sizeof(unsigned) * h->H));
 
     OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, nullptr, scaled, lamrows);
+    a.chunk_part = cpart;
+    a.cell_done = cdone;
     a.ubar = ubar;
     a.vbar = vbar;
     a.vsc = scaled ? vsc : vbar;
@@ -1216,6 +1302,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     // zero and the scalars from this call's values; every vector is written
     // before it is read (k_init, the start step of k_adj, k_upd)
     PDST_CUDA(cudaMemsetAsync(sy, 0, sizeof(LsqrSync), s));
+    PDST_CUDA(cudaMemsetAsync(cdone, 0, sizeof(unsigned) * h->H, s));
     LsqrScalars hs = init;
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
     k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, ubar, x, wv, partial, sc, sy);
@@ -1276,6 +1363,10 @@ extern "C" pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, d
         set_error("pdst_lsqr_noalloc: element indices were not built");
         return PDST_ERR_STATE;
     }
+    if (fmt == PDST_FMT_BLOCKED && !blocked_nz_ok(h->nz)) {
+        set_error("pdst_lsqr_noalloc: the blocked layout needs nz <= 64 (nz <= 32 unless nz %% 4 == 0)");
+        return PDST_ERR_LIMIT;
+    }
     const bool scaled = opts.precond == 1;
     if (scaled && !h->has_colscale) {
         set_error("pdst_lsqr_noalloc: precond = 1 needs pdst_set_col_scaling first");
@@ -1291,7 +1382,7 @@ extern "C" pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, d
     PDST_CHECK_ARG(kblock <= 1024, "pdst_lsqr_noalloc: kblock must be <= 1024");
     const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
     const size_t st = dtype == PDST_F64 ? sizeof(double) : sizeof(float);
-    const size_t need = noalloc_need(M, h->n, st);
+    const size_t need = noalloc_need(M, h->n, st, h->n_adj * h->nz, h->H);
     if (need > NOALLOC_BYTES) {
         set_error("pdst_lsqr_noalloc: this system needs %zu bytes of scratch; the static "
                   "array holds %zu (use pdst_lsqr)", need, NOALLOC_BYTES);

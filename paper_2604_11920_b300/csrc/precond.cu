@@ -27,14 +27,14 @@ constexpr double FEAT_EPS = 1e-8;   // floor inside the logarithms of the featur
 
 // ----------------------------------------------------------------- features
 
-// Pass 1, warp per column j = h*nz + k of G (CSC values, FP64 widening):
+// Pass 1, warp per column j = h*nz + k of G (blocked CSC values, FP64 widening):
 // f0 = log(||G_:j|| + eps), f1 = log(1 + rows), f2 = (k + 1/2)/nz,
 // f3 = sum G_rj^2 log T(r) / sum G_rj^2 (0 for an empty column),
 // f7 = log(max_r |G_rj| + eps).
 template <class VT>
 __global__ void k_feat1(int32_t n, int nz, const int64_t *__restrict__ cell_rptr,
                         const int32_t *__restrict__ cell_cnt, const int32_t *__restrict__ cell_rows,
-                        const VT *__restrict__ valT, const int32_t *__restrict__ row_period,
+                        const VT *__restrict__ valB, const int32_t *__restrict__ row_period,
                         const double *__restrict__ logT, float *feat) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -44,10 +44,10 @@ __global__ void k_feat1(int32_t n, int nz, const int64_t *__restrict__ cell_rptr
         const int k = (int)(j - h * nz);
         const int64_t c0 = cell_rptr[h];
         const int cnt = cell_cnt[h];
-        const VT *v = valT + (int64_t)nz * c0 + (int64_t)k * cnt;
+        const VT *v = valB + c0 * nz + k;
         double s2 = 0.0, st = 0.0, mx = 0.0;
         for (int q = lane; q < cnt; q += 32) {
-            const double g = (double)widen(v[q]);
+            const double g = (double)widen(v[(int64_t)q * nz]);
             const double g2 = g * g;
             s2 += g2;
             st += g2 * logT[row_period[cell_rows[c0 + q]]];
@@ -275,17 +275,17 @@ extern "C" pdst_status pdst_precond_features(pdst_handle_t h, const double *log_
     if (dtype == PDST_F64)
         k_feat1<double><<<grid, 256, 0, s>>>(h->n, h->nz, h->cell_rptr.as<int64_t>(),
                                             h->cell_cnt.as<int32_t>(), h->cell_rows.as<int32_t>(),
-                                            h->vals[0].csc.as<double>(), h->row_period.as<int32_t>(),
+                                            h->vals[0].bcsc.as<double>(), h->row_period.as<int32_t>(),
                                             logT.as<double>(), feat_dev);
     else if (dtype == PDST_F32)
         k_feat1<float><<<grid, 256, 0, s>>>(h->n, h->nz, h->cell_rptr.as<int64_t>(),
                                            h->cell_cnt.as<int32_t>(), h->cell_rows.as<int32_t>(),
-                                           h->vals[1].csc.as<float>(), h->row_period.as<int32_t>(),
+                                           h->vals[1].bcsc.as<float>(), h->row_period.as<int32_t>(),
                                            logT.as<double>(), feat_dev);
     else
         k_feat1<__nv_bfloat16><<<grid, 256, 0, s>>>(
             h->n, h->nz, h->cell_rptr.as<int64_t>(), h->cell_cnt.as<int32_t>(),
-            h->cell_rows.as<int32_t>(), h->vals[2].csc.as<__nv_bfloat16>(),
+            h->cell_rows.as<int32_t>(), h->vals[2].bcsc.as<__nv_bfloat16>(),
             h->row_period.as<int32_t>(), logT.as<double>(), feat_dev);
     k_feat2<<<grid, 256, 0, s>>>(h->n, h->grid.nx, h->grid.ny, h->nz, feat_dev);
     PDST_CUDA(cudaGetLastError());
