@@ -142,6 +142,13 @@ typedef struct {
     int32_t profile;   /* 1: one iteration per launch group, each kernel bracketed by CUDA
                           events; per-kernel device time returned in pdst_lsqr_info */
     double *rnorm_hist_dev; /* optional device array (itmax): ||r|| after each iteration */
+    int32_t refine;    /* > 0: mixed-precision iterative refinement with up to `refine`
+                          sweeps: m <- m + D argmin ||A_D dy - r(m)||, the residual r(m) of
+                          the augmented system computed in FP64 with the FP64 values of G
+                          (keep PDST_F64 in pdst_build_G), the correction solved by LSQR in
+                          `dtype` to tol (itmax per sweep).  0 (default): one solve. */
+    int32_t reserved2;
+    double refine_tol; /* refinement stops when ||D dy|| <= refine_tol ||m|| (default 1e-5) */
 } pdst_lsqr_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -163,6 +170,10 @@ typedef struct {
     double fwd_ms;   /* total device time of the forward kernel A v (profile = 1) */
     double adj_ms;   /* total device time of the adjoint kernel A^T u + recurrence */
     double upd_ms;   /* total device time of the x/w update kernel */
+    int32_t sweeps;  /* refinement sweeps performed (0 without refinement); iters is the
+                        total over all sweeps and the other fields describe the last one */
+    int32_t reserved;
+    double correction; /* ||last correction|| / ||m|| (refinement) */
 } pdst_lsqr_info;
 
 /*

@@ -503,14 +503,16 @@ __device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigne
 // beta_1 u_1 = [d; 0]: u-bar = [d; 0], beta_1 = ||d||, x = 0.
 template <class ST>
 __global__ void __launch_bounds__(LT) k_init(int64_t m, int64_t M, int32_t n,
-                                             const double *__restrict__ d, ST *ubar, double *x,
+                                             const double *__restrict__ d,
+                                             const double *__restrict__ baug, ST *ubar, double *x,
                                              double *wv, double *partial, LsqrScalars *sc,
                                              LsqrSync *sy) {
     double ss = 0.0;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = t0; i < M; i += st) {
-        double v = i < m ? d[i] : 0.0;
+        // b = [d; 0], or a full augmented right-hand side (refinement sweeps)
+        double v = baug ? baug[i] : (i < m ? d[i] : 0.0);
         ubar[i] = (ST)v;
         ss += v * v;
     }
@@ -662,10 +664,12 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
 }
 
 __global__ void k_finalize(int32_t n, const double *__restrict__ x, const double *__restrict__ D,
-                           double *m_out) {
+                           double *m_out, int accumulate = 0) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x)
-        m_out[j] = D ? D[j] * x[j] : x[j];
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = D ? D[j] * x[j] : x[j];
+        m_out[j] = accumulate ? m_out[j] + v : v;
+    }
 }
 
 // y = G x or G^T x with FP64 vectors (pdst_apply_G).
@@ -730,6 +734,7 @@ struct LsqrWork {
     const void *graph_D = nullptr;
     int64_t M = 0;
     DevBuf ubar, vbar, vsc, x, wv, partial, scal, sync, chunk_part, cell_done;
+    DevBuf ones, baug, corr;         // refinement: unit scaling, augmented residual, norms
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
     std::map<int, cudaGraphExec_t> graphs;   // key: kblock
@@ -860,15 +865,18 @@ template <class VT, class ST, int FMT> struct Solver {
 
     static pdst_status run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                            const double *d, const LsqrScalars &init, int kblock, bool use_graph,
-                           bool profile, double *m_out, cudaStream_t s, RunStats &rs) {
+                           bool profile, double *m_out, cudaStream_t s, RunStats &rs,
+                           const double *baug = nullptr, bool accumulate = false,
+                           const double *Dover = nullptr) {
         OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, scaled, lamrows);
+        if (Dover) a.D = Dover;
         PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
         PDST_CUDA(cudaMemsetAsync(w->cell_done.p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
         *w->h_scal = init;
         PDST_CUDA(cudaMemcpyAsync(w->scal.p, w->h_scal, sizeof(LsqrScalars),
                                   cudaMemcpyHostToDevice, s));
         unsigned ginit = persistent_grid(k_init<ST>, h->device, w->M);
-        k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, a.ubar, a.x, a.wv, a.partial, a.sc,
+        k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, baug, a.ubar, a.x, a.wv, a.partial, a.sc,
                                         a.sy);
         k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
@@ -916,7 +924,7 @@ template <class VT, class ST, int FMT> struct Solver {
                 rs.launches += 3 * kblock;
             }
         }
-        k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out);
+        k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out, accumulate ? 1 : 0);
         PDST_CUDA(cudaGetLastError());
         rs.launches += 1;
         PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
@@ -931,10 +939,71 @@ template <class VT, class ST, int FMT>
 static pdst_status dispatch_run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                                 const double *d, const LsqrScalars &init, int kblock,
                                 bool use_graph, bool profile, double *m_out, cudaStream_t s,
-                                bool fresh, RunStats &rs) {
+                                bool fresh, RunStats &rs, const double *baug = nullptr,
+                                bool accumulate = false, const double *Dover = nullptr) {
     if (fresh) PDST_TRY((Solver<VT, ST, FMT>::prepare(h, w, lamrows)));
     return Solver<VT, ST, FMT>::run(h, w, dtype, scaled, lamrows, d, init, kblock, use_graph,
-                                    profile, m_out, s, rs);
+                                    profile, m_out, s, rs, baug, accumulate, Dover);
+}
+
+// ------------------------------------------------ mixed-precision refinement
+
+// FP64 residual of the augmented system at the current model m:
+// baug = [d - G m; -w L m; -lam m] (lam rows only when lamrows).
+template <int FMT>
+__global__ void __launch_bounds__(LT) k_resid(OpArgs<double, double> a, const double *__restrict__ d,
+                                              const double *__restrict__ mv, double w, double lam,
+                                              int lamrows, double *baug) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = gw; r < a.m; r += nw) {
+        const double y = FMT == FMT_ELEM
+                             ? dot_elem<double, double, double>(a.row_ptr, a.col, a.val, mv, r, lane)
+                             : dot_blk_row<double, double, double>(a.row_cptr, a.row_cells, a.val,
+                                                                   mv, r, a.nz, lane);
+        if (lane == 0) baug[r] = d[r] - y;
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        baug[a.m + j] = -w * laplace<double, double>(mv, j, a.nx, a.ny, a.nz);
+        if (lamrows) baug[a.m + a.n + j] = -lam * mv[j];
+    }
+}
+
+// out[0] = ||D x||^2, out[1] = ||m||^2 (one block, fixed order).
+__global__ void k_corr_norms(int32_t n, const double *__restrict__ x, const double *__restrict__ D,
+                             const double *__restrict__ mv, double *out) {
+    __shared__ double s0[32], s1[32];
+    double a = 0.0, b = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double c = D ? D[j] * x[j] : x[j];
+        a += c * c;
+        b += mv[j] * mv[j];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s0[warp] = a;
+        s1[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            ta += s0[i];
+            tb += s1[i];
+        }
+        out[0] = ta;
+        out[1] = tb;
+    }
+}
+
+__global__ void k_fill(int64_t n, double v, double *x) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        x[j] = v;
 }
 
 static bool blocked_nz_ok(int nz) { return (nz % 4 == 0) ? nz <= 64 : nz <= 32; }
@@ -966,15 +1035,26 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         set_error("pdst_lsqr: the blocked layout needs nz <= 64 (nz <= 32 unless nz %% 4 == 0)");
         return PDST_ERR_LIMIT;
     }
-    const bool scaled = opts.precond == 1;
-    if (scaled && !h->has_colscale) {
+    const bool user_scaled = opts.precond == 1;
+    if (user_scaled && !h->has_colscale) {
         set_error("pdst_lsqr: precond = 1 needs pdst_set_col_scaling first");
         return PDST_ERR_STATE;
     }
     PDST_CHECK_ARG(opts.precond == 0 || opts.precond == 1, "pdst_lsqr: unknown precond %d",
                    opts.precond);
+    PDST_CHECK_ARG(opts.refine >= 0 && opts.refine <= 100, "pdst_lsqr: refine must be in 0..100");
+    const bool refine = opts.refine > 0;
+    if (refine && !h->vals[PDST_F64].present) {
+        set_error("pdst_lsqr: refinement needs the FP64 values (keep PDST_F64 in pdst_build_G)");
+        return PDST_ERR_STATE;
+    }
+    PDST_CHECK_ARG(!(refine && opts.profile), "pdst_lsqr: profile and refine are exclusive");
+    // refinement sweeps solve for a correction with a full augmented right-hand
+    // side, so they always use the form with explicit lambda rows (unit scaling
+    // when none is set)
+    const bool scaled = user_scaled || refine;
     const bool lamrows = scaled && lam > 0.0;
-    const int kblock = opts.kblock > 0 ? opts.kblock : 16;
+    const int kblock = opts.profile ? 1 : (opts.kblock > 0 ? opts.kblock : 16);
     PDST_CHECK_ARG(kblock <= 1024, "pdst_lsqr: kblock must be <= 1024");
 
     LsqrScalars init{};
@@ -992,36 +1072,101 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     if (!h->work) h->work = new LsqrWork();
     LsqrWork *w = h->work;
     const bool fresh = w->dtype != dtype || w->format != fmt || w->lamrows != (int)lamrows;
+    const double *Dover = nullptr;
+    if (refine && !user_scaled) {
+        PDST_TRY(w->ones.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+        k_fill<<<num_sms(h->device) * 4, LT, 0, s>>>(h->n, 1.0, w->ones.as<double>());
+        PDST_CUDA(cudaGetLastError());
+        Dover = w->ones.as<double>();
+    }
     // captured graphs hold the workspace and scaling pointers: rebuild on change
-    const void *dptr = scaled ? h->colscale.p : nullptr;
+    const void *dptr = Dover ? (const void *)Dover : (user_scaled ? h->colscale.p : nullptr);
     if (fresh || w->graph_D != dptr) {
         for (auto &g : w->graphs)
             if (g.second) cudaGraphExecDestroy(g.second);
         w->graphs.clear();
         w->graph_D = dptr;
     }
-    pdst_status st;
     const bool ug = opts.use_graph != 0;
     const bool prof = opts.profile != 0;
     RunStats rs;
-    if (dtype == PDST_F64) {
-        st = fmt == PDST_FMT_ELEMENT
-                 ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                         kblock, ug, prof, m_out, s, fresh, rs)
-                 : dispatch_run<double, double, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                        kblock, ug, prof, m_out, s, fresh, rs);
-    } else if (dtype == PDST_F32) {
-        st = fmt == PDST_FMT_ELEMENT
-                 ? dispatch_run<float, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                       kblock, ug, prof, m_out, s, fresh, rs)
-                 : dispatch_run<float, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
-                                                      kblock, ug, prof, m_out, s, fresh, rs);
+
+    auto solve_once = [&](const double *baug, bool accumulate, bool fresh_) -> pdst_status {
+        if (dtype == PDST_F64)
+            return fmt == PDST_FMT_ELEMENT
+                       ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
+                                                               init, kblock, ug, prof, m_out, s,
+                                                               fresh_, rs, baug, accumulate, Dover)
+                       : dispatch_run<double, double, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev,
+                                                              init, kblock, ug, prof, m_out, s,
+                                                              fresh_, rs, baug, accumulate, Dover);
+        if (dtype == PDST_F32)
+            return fmt == PDST_FMT_ELEMENT
+                       ? dispatch_run<float, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
+                                                             init, kblock, ug, prof, m_out, s,
+                                                             fresh_, rs, baug, accumulate, Dover)
+                       : dispatch_run<float, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev,
+                                                            init, kblock, ug, prof, m_out, s,
+                                                            fresh_, rs, baug, accumulate, Dover);
+        return fmt == PDST_FMT_ELEMENT
+                   ? dispatch_run<__nv_bfloat16, float, FMT_ELEM>(h, w, dtype, scaled, lamrows,
+                                                                 d_dev, init, kblock, ug, prof,
+                                                                 m_out, s, fresh_, rs, baug,
+                                                                 accumulate, Dover)
+                   : dispatch_run<__nv_bfloat16, float, FMT_BLK>(h, w, dtype, scaled, lamrows,
+                                                                d_dev, init, kblock, ug, prof,
+                                                                m_out, s, fresh_, rs, baug,
+                                                                accumulate, Dover);
+    };
+
+    pdst_status st = PDST_OK;
+    int total_iters = 0, sweeps = 0;
+    double correction = 0.0;
+    if (!refine) {
+        st = solve_once(nullptr, false, fresh);
+        total_iters = w->h_scal ? w->h_scal->itn : 0;
     } else {
-        st = fmt == PDST_FMT_ELEMENT
-                 ? dispatch_run<__nv_bfloat16, float, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
-                                                               init, kblock, ug, prof, m_out, s, fresh, rs)
-                 : dispatch_run<__nv_bfloat16, float, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev,
-                                                              init, kblock, ug, prof, m_out, s, fresh, rs);
+        // mixed-precision refinement: m <- m + D * argmin ||A_D dy - r(m)||, with the
+        // residual r(m) of the augmented system in FP64 (FP64 values of G) and the
+        // correction from the reduced-precision LSQR
+        const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
+        PDST_TRY(w->baug.alloc(sizeof(double) * std::max<int64_t>(M, 1)));
+        PDST_TRY(w->corr.alloc(sizeof(double) * 2));
+        PDST_CUDA(cudaMemsetAsync(m_out, 0, sizeof(double) * h->n, s));
+        const double rtol = opts.refine_tol > 0.0 ? opts.refine_tol : 1e-5;
+        const bool elem64 = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
+        auto a64 = make_args<double, double>(h, PDST_F64, nullptr, false, false);
+        const unsigned gres = persistent_grid(elem64 ? k_resid<FMT_ELEM> : k_resid<FMT_BLK>,
+                                              h->device, (h->m + h->n) * 32);
+        bool fr = fresh;
+        for (int sweep = 0; sweep < opts.refine; ++sweep) {
+            if (elem64)
+                k_resid<FMT_ELEM><<<gres, LT, 0, s>>>(a64, d_dev, m_out, w_s, lam, lamrows ? 1 : 0,
+                                                      w->baug.as<double>());
+            else
+                k_resid<FMT_BLK><<<gres, LT, 0, s>>>(a64, d_dev, m_out, w_s, lam, lamrows ? 1 : 0,
+                                                     w->baug.as<double>());
+            PDST_CUDA(cudaGetLastError());
+            rs.launches += 1;
+            st = solve_once(w->baug.as<double>(), true, fr);
+            fr = false;
+            if (st != PDST_OK) break;
+            w->dtype = dtype;
+            w->format = fmt;
+            w->lamrows = (int)lamrows;
+            total_iters += w->h_scal->itn;
+            ++sweeps;
+            if (w->h_scal->err) break;
+            const double *Dp = Dover ? Dover : h->colscale.as<double>();
+            k_corr_norms<<<1, 1024, 0, s>>>(h->n, w->x.as<double>(), Dp, m_out,
+                                            w->corr.as<double>());
+            rs.launches += 1;
+            double cn[2];
+            PDST_CUDA(cudaMemcpyAsync(cn, w->corr.p, sizeof(cn), cudaMemcpyDeviceToHost, s));
+            PDST_CUDA(cudaStreamSynchronize(s));
+            correction = cn[1] > 0.0 ? std::sqrt(cn[0] / cn[1]) : 0.0;
+            if (correction <= rtol || w->h_scal->itn == 0) break;
+        }
     }
     if (st != PDST_OK) {
         w->dtype = -1;
@@ -1032,7 +1177,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     w->lamrows = (int)lamrows;
     const LsqrScalars &c = *w->h_scal;
     if (info) {
-        info->iters = c.itn;
+        info->iters = total_iters;
         info->istop = c.istop;
         info->rnorm = c.rnorm;
         info->arnorm = c.arnorm;
@@ -1045,6 +1190,8 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         info->fwd_ms = rs.fwd_ms;
         info->adj_ms = rs.adj_ms;
         info->upd_ms = rs.upd_ms;
+        info->sweeps = sweeps;
+        info->correction = correction;
     }
     if (c.err) {
         set_error("pdst_lsqr: non-finite value in the LSQR recurrence (iteration %d)", c.itn);
@@ -1126,6 +1273,8 @@ extern "C" void pdst_lsqr_opts_default(pdst_lsqr_opts *o) {
     o->use_graph = 1;
     o->profile = 0;
     o->rnorm_hist_dev = nullptr;
+    o->refine = 0;
+    o->refine_tol = 1e-5;
 }
 
 extern "C" pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lambda,
@@ -1305,7 +1454,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     PDST_CUDA(cudaMemsetAsync(cdone, 0, sizeof(unsigned) * h->H, s));
     LsqrScalars hs = init;
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
-    k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, ubar, x, wv, partial, sc, sy);
+    k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, nullptr, ubar, x, wv, partial, sc, sy);
     k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 1);
     k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, partial, sc, sy);
     PDST_CUDA(cudaGetLastError());

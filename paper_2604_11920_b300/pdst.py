@@ -48,7 +48,9 @@ class LsqrOpts(ctypes.Structure):
                 ("atol", ctypes.c_double), ("btol", ctypes.c_double),
                 ("conlim", ctypes.c_double), ("precond", ctypes.c_int32),
                 ("kblock", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p),
+                ("refine", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("refine_tol", ctypes.c_double)]
 
 
 class BatchedOpts(ctypes.Structure):
@@ -64,7 +66,8 @@ class LsqrInfo(ctypes.Structure):
                 ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int32), ("profiled_iters", ctypes.c_int32),
                 ("fwd_ms", ctypes.c_double), ("adj_ms", ctypes.c_double),
-                ("upd_ms", ctypes.c_double)]
+                ("upd_ms", ctypes.c_double), ("sweeps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("correction", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -153,7 +156,8 @@ def _np_ptr(a: np.ndarray):
 
 
 def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, precond=0,
-              kblock=16, use_graph=True, hist=None, profile=False) -> LsqrOpts:
+              kblock=16, use_graph=True, hist=None, profile=False, refine=0,
+              refine_tol=1e-5) -> LsqrOpts:
     o = LsqrOpts()
     load().pdst_lsqr_opts_default(ctypes.byref(o))
     o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -161,6 +165,7 @@ def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, prec
     o.atol, o.btol, o.conlim = atol, btol, conlim
     o.precond, o.kblock, o.use_graph = int(precond), int(kblock), int(bool(use_graph))
     o.profile = int(bool(profile))
+    o.refine, o.refine_tol = int(refine), float(refine_tol)
     o.rnorm_hist_dev = None if hist is None else hist.data_ptr()
     return o
 
