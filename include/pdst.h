@@ -142,13 +142,15 @@ typedef struct {
     int32_t profile;   /* 1: one iteration per launch group, each kernel bracketed by CUDA
                           events; per-kernel device time returned in pdst_lsqr_info */
     double *rnorm_hist_dev; /* optional device array (itmax): ||r|| after each iteration */
-    int32_t refine;    /* > 0: mixed-precision iterative refinement with up to `refine`
-                          sweeps: m <- m + D argmin ||A_D dy - r(m)||, the residual r(m) of
-                          the augmented system computed in FP64 with the FP64 values of G
-                          (keep PDST_F64 in pdst_build_G), the correction solved by LSQR in
-                          `dtype` to tol (itmax per sweep).  0 (default): one solve. */
-    int32_t reserved2;
-    double refine_tol; /* refinement stops when ||D dy|| <= refine_tol ||m|| (default 1e-5) */
+    int32_t refine;    /* > 0: refinement with up to `refine` sweeps:
+                          m <- m + D argmin ||A_D dy - r(m)||, the residual r(m) of the
+                          augmented system computed in FP64 with the FP64 values of G (keep
+                          PDST_F64 in pdst_build_G).  Sweep 0 solves in `dtype` to tol;
+                          later sweeps solve in refine_dtype with atol = btol = refine_tol
+                          (the stopping rules then hold for the full problem at m).  Stops
+                          early when a sweep needs no iteration.  0 (default): one solve. */
+    int32_t refine_dtype; /* pdst_dtype of sweeps 1.. (-1, default: dtype) */
+    double refine_tol; /* tolerance of sweeps 1.. (default 1e-5) */
 } pdst_lsqr_opts;
 
 /* Fill *o with the defaults listed above. */

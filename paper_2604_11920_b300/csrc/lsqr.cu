@@ -1044,6 +1044,12 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
                    opts.precond);
     PDST_CHECK_ARG(opts.refine >= 0 && opts.refine <= 100, "pdst_lsqr: refine must be in 0..100");
     const bool refine = opts.refine > 0;
+    PDST_CHECK_ARG(opts.refine_dtype >= -1 && opts.refine_dtype <= 2,
+                   "pdst_lsqr: unknown refine_dtype %d", opts.refine_dtype);
+    if (refine && opts.refine_dtype >= 0 && !h->vals[opts.refine_dtype].present) {
+        set_error("pdst_lsqr: values of refine_dtype %d were not kept", opts.refine_dtype);
+        return PDST_ERR_STATE;
+    }
     if (refine && !h->vals[PDST_F64].present) {
         set_error("pdst_lsqr: refinement needs the FP64 values (keep PDST_F64 in pdst_build_G)");
         return PDST_ERR_STATE;
@@ -1091,7 +1097,8 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     const bool prof = opts.profile != 0;
     RunStats rs;
 
-    auto solve_once = [&](const double *baug, bool accumulate, bool fresh_) -> pdst_status {
+    auto solve_once = [&](const double *baug, bool accumulate, bool fresh_,
+                          int dtype) -> pdst_status {
         if (dtype == PDST_F64)
             return fmt == PDST_FMT_ELEMENT
                        ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,
@@ -1123,7 +1130,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     int total_iters = 0, sweeps = 0;
     double correction = 0.0;
     if (!refine) {
-        st = solve_once(nullptr, false, fresh);
+        st = solve_once(nullptr, false, fresh, dtype);
         total_iters = w->h_scal ? w->h_scal->itn : 0;
     } else {
         // mixed-precision refinement: m <- m + D * argmin ||A_D dy - r(m)||, with the
@@ -1139,7 +1146,16 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         const unsigned gres = persistent_grid(elem64 ? k_resid<FMT_ELEM> : k_resid<FMT_BLK>,
                                               h->device, (h->m + h->n) * 32);
         bool fr = fresh;
+        const int rdtype = opts.refine_dtype >= 0 ? opts.refine_dtype : dtype;
+        int cur_dtype = dtype;
         for (int sweep = 0; sweep < opts.refine; ++sweep) {
+            // sweep 0 in dtype at tol; later sweeps in refine_dtype at refine_tol
+            const int sd = sweep == 0 ? dtype : rdtype;
+            if (sweep == 1) {
+                init.atol = init.btol = rtol;
+                if (sd != cur_dtype) fr = true;
+            }
+            cur_dtype = sd;
             if (elem64)
                 k_resid<FMT_ELEM><<<gres, LT, 0, s>>>(a64, d_dev, m_out, w_s, lam, lamrows ? 1 : 0,
                                                       w->baug.as<double>());
@@ -1148,10 +1164,15 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
                                                      w->baug.as<double>());
             PDST_CUDA(cudaGetLastError());
             rs.launches += 1;
-            st = solve_once(w->baug.as<double>(), true, fr);
+            if (fr && w->dtype != sd) {
+                for (auto &g : w->graphs)
+                    if (g.second) cudaGraphExecDestroy(g.second);
+                w->graphs.clear();
+            }
+            st = solve_once(w->baug.as<double>(), true, fr || w->dtype != sd, sd);
             fr = false;
             if (st != PDST_OK) break;
-            w->dtype = dtype;
+            w->dtype = sd;
             w->format = fmt;
             w->lamrows = (int)lamrows;
             total_iters += w->h_scal->itn;
@@ -1165,14 +1186,15 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
             PDST_CUDA(cudaMemcpyAsync(cn, w->corr.p, sizeof(cn), cudaMemcpyDeviceToHost, s));
             PDST_CUDA(cudaStreamSynchronize(s));
             correction = cn[1] > 0.0 ? std::sqrt(cn[0] / cn[1]) : 0.0;
-            if (correction <= rtol || w->h_scal->itn == 0) break;
+            if (sweep > 0 && (correction <= 1e-3 * rtol || w->h_scal->itn == 0)) break;
         }
+        w->dtype = cur_dtype;
     }
     if (st != PDST_OK) {
         w->dtype = -1;
         return st;
     }
-    w->dtype = dtype;
+    if (!refine) w->dtype = dtype;
     w->format = fmt;
     w->lamrows = (int)lamrows;
     const LsqrScalars &c = *w->h_scal;
@@ -1274,6 +1296,7 @@ extern "C" void pdst_lsqr_opts_default(pdst_lsqr_opts *o) {
     o->profile = 0;
     o->rnorm_hist_dev = nullptr;
     o->refine = 0;
+    o->refine_dtype = -1;
     o->refine_tol = 1e-5;
 }
 

@@ -49,7 +49,7 @@ class LsqrOpts(ctypes.Structure):
                 ("conlim", ctypes.c_double), ("precond", ctypes.c_int32),
                 ("kblock", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p),
-                ("refine", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("refine_dtype", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double)]
 
 
@@ -157,7 +157,7 @@ def _np_ptr(a: np.ndarray):
 
 def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, precond=0,
               kblock=16, use_graph=True, hist=None, profile=False, refine=0,
-              refine_tol=1e-5) -> LsqrOpts:
+              refine_tol=1e-5, refine_dtype=None) -> LsqrOpts:
     o = LsqrOpts()
     load().pdst_lsqr_opts_default(ctypes.byref(o))
     o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -166,6 +166,9 @@ def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, prec
     o.precond, o.kblock, o.use_graph = int(precond), int(kblock), int(bool(use_graph))
     o.profile = int(bool(profile))
     o.refine, o.refine_tol = int(refine), float(refine_tol)
+    o.refine_dtype = -1 if refine_dtype is None else (DTYPES[refine_dtype]
+                                                      if isinstance(refine_dtype, str)
+                                                      else int(refine_dtype))
     o.rnorm_hist_dev = None if hist is None else hist.data_ptr()
     return o
 
