@@ -51,7 +51,8 @@ PLAIN = "f64-element"
 MODEL_PATH = os.path.join(ROOT, "paper_2604_11920_b300", "precond_mlp.json")
 DEFAULT_FORM = "f32-blocked-learned" if os.path.exists(MODEL_PATH) else "f32-blocked-colnorm"
 ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
-TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9)
+TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10)
+REF_TOL = 1e-12                       # FP64 reference solve (stops earlier on S4-S6 if need be)
 VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
 VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4}
 
@@ -308,8 +309,8 @@ def run_pdst(args, rank, world):
     else:
         ms_plain, res_plain = ms, res
     m_plain = res_plain.m.clone()
-    # FP64 reference solution: plain form at tol 1e-10 (its iteration count is reported)
-    ref = h.lsqr(d, p.w, p.lam, 100000, 1e-10, dtype="f64", fmt="element")
+    # FP64 reference solution: plain form at tol REF_TOL (its iteration count is reported)
+    ref = h.lsqr(d, p.w, p.lam, 200000, REF_TOL, dtype="f64", fmt="element")
 
     def relerr(a):
         return float(torch.linalg.norm(a - ref.m) / torch.linalg.norm(ref.m))
@@ -397,7 +398,7 @@ def run_pdst(args, rank, world):
                "d2h_bytes_per_step": 8 * h.n}
 
     out.update({
-        "reference": {"form": PLAIN, "tol": 1e-10, "iters": ref.info["iters"],
+        "reference": {"form": PLAIN, "tol": REF_TOL, "iters": ref.info["iters"],
                       "istop": ref.info["istop"]},
         "config": {"workload": workload_desc(p), "form": args.form,
                    "plain_form": PLAIN, "nnz": h.nnz,
