@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-workload section (64 systems x 16 right-hand sides)")
     ap.add_argument("--batched-systems", type=int, default=64)
+    ap.add_argument("--only-batched", action="store_true",
+                    help="print the batched-workload section alone")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the chosen form only (for profiler runs)")
     ap.add_argument("--ncu-case", action="store_true",
@@ -567,6 +569,10 @@ def main():
             run_reference(args, rank, world)
         elif args.ncu_case:
             run_ncu_case(args)
+        elif args.only_batched:
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps(batched_section(args.batched_systems, steps=args.steps)))
         else:
             run_pdst(args, rank, world)
     finally:

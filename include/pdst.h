@@ -244,11 +244,11 @@ pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev, double w,
 
 typedef struct {
     int32_t tile_rows;        /* G rows per forward work item; 0 = chosen by the autotuner,
-                                 which times the forward phase for 2, 8 and 32 rows */
+                                 which times one whole iteration for 2, 8 and 32 rows */
     int32_t kblock;           /* iterations per graph launch (<= 0: 8) */
     int32_t chosen_tile_rows; /* out: the tile used by the call */
     int32_t kernel_launches;  /* out: kernels launched by the call (graph nodes included) */
-    double tune_ms[4];        /* out: forward-phase time per autotuner candidate (ms) */
+    double tune_ms[4];        /* out: iteration time per autotuner candidate (ms) */
 } pdst_batched_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -267,7 +267,8 @@ void pdst_batched_opts_default(pdst_batched_opts *o);
  * d_dev[s]: m_s x nrhs[s] FP64 (device), right-hand side fastest.
  * w[s]: smoothing weight per system.  lambda[s]: nrhs[s] damping values (host).
  * m_out_dev[s]: n_s x nrhs[s] FP64 (device, caller-owned), right-hand side
- * fastest.  infos: sum(nrhs) entries, system-major (may be NULL).  dtype:
+ * fastest.  infos: sum(nrhs) entries, system-major (may be NULL).  Each
+ * system needs nz <= 16 (PDST_ERR_LIMIT otherwise).  dtype:
  * values and u/v vectors (PDST_F32 / PDST_BF16 use FP32 vectors).  opts may be
  * NULL (autotuned tile, kblock 8); its out fields are filled when given.
  * Work space for the batch is allocated on the first call and reused while the

@@ -31,6 +31,7 @@ namespace {
 constexpr int BT = 256;      // threads per block
 constexpr int RMAX = 16;     // right-hand sides per system (lanes of a half-warp)
 constexpr int LCOLS = 32;    // columns per stencil / update work item
+constexpr int NB = 6;        // work buffers per system: U, V, X, W, chunk sums, chunk counters
 
 template <class VT, class ST> struct BSys {
     int64_t m;
@@ -44,8 +45,11 @@ template <class VT, class ST> struct BSys {
     const int32_t *cell_rows;
     const int32_t *cell_order;
     const VT *valB;   // blocked CSC values
+    const int32_t *adj_item;   // (cell, first row) per adjoint work item
+    ST *chunk_part;   // adjoint work items x nz x RMAX partial sums
+    unsigned *cell_done;       // H finished-chunk counters
     ST *U;            // (m + n) x R, right-hand side fastest
-    ST *V;            // n x R
+    ST *V;            // R x n, right-hand side major
     double *X, *W;    // n x R
     const double *d;  // m x R
     LsqrScalars *sc;  // R
@@ -100,7 +104,7 @@ __device__ __forceinline__ AT laplace_strided(const ST *__restrict__ x, int64_t 
     return s;
 }
 
-// u-bar = [d; 0], x = w = 0; partials of ||d_j||^2.
+// u-bar = [d; 0], v = x = w = 0; partials of ||d_j||^2.
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                               int64_t nitems, int TR, double *partial) {
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 for (int64_t c = c0 + half; c < c1; c += 2) {
                     S.U[(S.m + c) * R + j] = (ST)0;
-                    S.V[c * R + j] = (ST)0;
+                    S.V[(int64_t)j * S.n + c] = (ST)0;
                     S.X[c * R + j] = 0.0;
                     S.W[c * R + j] = 0.0;
                 }
@@ -137,8 +141,17 @@ __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const
     }
 }
 
-// Forward phase: G rows (half-warp per row, lanes = right-hand sides) and the
-// w L rows (stencil tiles) of every active system.
+// Laplacian of column jc of one right-hand side stored contiguously (x[c]).
+template <class AT, class ST>
+__device__ __forceinline__ AT laplace_col(const ST *__restrict__ x, int64_t jc, int nx, int ny,
+                                          int nz) {
+    return laplace<AT, ST>(x, jc, nx, ny, nz);
+}
+
+// Forward phase: G rows (half-warp per row, lane j = right-hand side j; V is
+// stored right-hand-side major, so each lane reads its column's nz entries of
+// a run as nz/4 16-byte vectors; the row's first 64 cells are read into
+// registers once and broadcast by shuffle) and the w L rows (column tiles).
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int TR, double *partial) {
@@ -157,27 +170,51 @@ __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const 
             const Col c = col_state(S.sc, j, R);
             const AT ia = c.alpha > 0.0 ? (AT)(1.0 / c.alpha) : (AT)0;
             const AT cu = c.beta > 0.0 ? (AT)(c.alpha / c.beta) : (AT)0;
+            const ST *Vj = S.V + (int64_t)jj * S.n;
             if (li < S.nf) {
                 const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
-                for (int64_t r = r0 + half; r < r1; r += 2) {
-                    const int64_t e0 = __ldg(S.row_cptr + r), e1 = __ldg(S.row_cptr + r + 1);
+                // both halves iterate the same number of times (shuffles below)
+                const int64_t nrows = (r1 - r0 + 1) / 2;
+                for (int64_t t = 0; t < nrows; ++t) {
+                    const int64_t r = r0 + 2 * t + half;
+                    const bool live = r < r1;
+                    int64_t e0 = 0, e1 = 0;
+                    if (live) {
+                        e0 = __ldg(S.row_cptr + r);
+                        e1 = __ldg(S.row_cptr + r + 1);
+                    }
+                    const int nrun = (int)(e1 - e0);
+                    int cc[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        cc[i] = (j + 16 * i < nrun) ? __ldg(S.row_cells + e0 + j + 16 * i) : 0;
+                    // the two halves may have different run counts: loop to the max
+                    int nmax = nrun;
+                    nmax = max(nmax, __shfl_xor_sync(FULL, nmax, 16));
                     AT acc = 0;
-                    for (int64_t e = e0; e < e1; ++e) {
-                        const int h = __ldg(S.row_cells + e);
-                        const VT *v = S.val + e * nz;
-                        const ST *vb = S.V + (int64_t)h * nz * R + jj;
+                    for (int e = 0; e < nmax; ++e) {
+                        const int src = (half << 4) | (e & 15);
+                        const int ci = e >> 4;
+                        int h = __shfl_sync(FULL, ci == 0 ? cc[0] : ci == 1 ? cc[1]
+                                                        : ci == 2 ? cc[2] : cc[3], src);
+                        if (e >= nrun) continue;
+                        if (e >= 64) h = __ldg(S.row_cells + e0 + e);
+                        const VT *v = S.val + (e0 + e) * nz;
+                        const ST *xb = Vj + (int64_t)h * nz;
                         if ((nz & 3) == 0) {
                             for (int k = 0; k < nz; k += 4) {
                                 typename Wide<VT>::T q[4];
+                                ST xv[4];
                                 Pack4<VT>::ld(v + k, q);
-                                acc += (AT)q[0] * (AT)vb[(k + 0) * R] + (AT)q[1] * (AT)vb[(k + 1) * R] +
-                                       (AT)q[2] * (AT)vb[(k + 2) * R] + (AT)q[3] * (AT)vb[(k + 3) * R];
+                                ldx4<ST>(xb + k, xv);
+                                acc += (AT)q[0] * (AT)xv[0] + (AT)q[1] * (AT)xv[1] +
+                                       (AT)q[2] * (AT)xv[2] + (AT)q[3] * (AT)xv[3];
                             }
                         } else {
-                            for (int k = 0; k < nz; ++k) acc += (AT)widen(v[k]) * (AT)vb[k * R];
+                            for (int k = 0; k < nz; ++k) acc += (AT)widen(v[k]) * (AT)xb[k];
                         }
                     }
-                    if (c.act) {
+                    if (live && c.act) {
                         const AT u = acc * ia - cu * S.U[r * R + j];
                         S.U[r * R + j] = u;
                         ss += (double)u * (double)u;
@@ -188,7 +225,7 @@ __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const 
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 const AT wsm = (AT)S.w;
                 for (int64_t jc = c0 + half; jc < c1; jc += 2) {
-                    const AT lap = laplace_strided<AT, ST>(S.V, jc, R, jj, S.nx, S.ny, nz);
+                    const AT lap = laplace_col<AT, ST>(Vj, jc, S.nx, S.ny, nz);
                     if (c.act) {
                         ST *up = S.U + (S.m + jc) * R + j;
                         const AT u = wsm * lap * ia - cu * *up;
@@ -203,9 +240,13 @@ __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const 
     }
 }
 
-// Adjoint phase: work item = (cell, group of up to four depths) of one
-// system, cells longest first; the two half-warps take alternate rows of the
-// cell, lanes = right-hand sides.
+constexpr int BNZ = 16;   // depths per cell handled in registers by the adjoint
+
+// Adjoint phase: work item = a chunk of up to ADJ_CHUNK rows of one cell of
+// one system (the handle's adjoint work list).  Lane j = right-hand side j;
+// the two half-warps take alternate rows; each row's index and u are read
+// once and its nz values as nz/4 16-byte vectors (blocked CSC).  A cell split
+// over several chunks is finished by its last chunk (chunk order sums).
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int init, double *partial) {
@@ -213,6 +254,8 @@ __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const 
     const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ int last_flag[BT / 32];
+    const int warp = threadIdx.x >> 5;
     for (int64_t it = gw; it < nitems; it += nw) {
         const int s = find_sys(beg, nsys, it);
         const BSys<VT, ST> &S = sys[s];
@@ -225,44 +268,78 @@ __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const 
             const bool upd = c.act && (init || c.beta > 0.0);
             const AT ib = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
             const AT cv = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
-            const int kg = (nz + 3) >> 2;
-            const int h = __ldg(S.cell_order + li / kg);
-            const int k0 = 4 * (int)(li % kg);
-            const int nk = nz - k0 < 4 ? nz - k0 : 4;
+            const int h = __ldg(S.adj_item + 2 * li);
+            const int q0 = __ldg(S.adj_item + 2 * li + 1);
             const int64_t c0 = __ldg(S.cell_rptr + h);
             const int cnt = __ldg(S.cell_cnt + h);
-            const VT *vb = S.valB + c0 * nz + k0;
+            const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
             const int32_t *rows = S.cell_rows + c0;
-            AT acc[4] = {0, 0, 0, 0};
-            for (int q = half; q < cnt; q += 2) {
-                const int r = __ldg(rows + q);
-                const AT ur = (AT)S.U[(int64_t)r * R + jj];
-                if (nk == 4 && (nz & 3) == 0) {
-                    typename Wide<VT>::T w4[4];
-                    Pack4<VT>::ld(vb + (int64_t)q * nz, w4);
+            const VT *vb = S.valB + c0 * nz;
+            AT acc[BNZ];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) acc[t] += (AT)w4[t] * ur;
+            for (int k = 0; k < BNZ; ++k) acc[k] = 0;
+            int rnext = (q0 + half < q1) ? __ldg(rows + q0 + half) : -1;
+            for (int q = q0 + half; q < q1; q += 2) {
+                const int r = rnext;
+                rnext = (q + 2 < q1) ? __ldg(rows + q + 2) : -1;
+                const AT ur = (AT)S.U[(int64_t)r * R + jj];
+                const VT *v = vb + (int64_t)q * nz;
+                if ((nz & 3) == 0) {
+#pragma unroll
+                    for (int k = 0; k < BNZ; k += 4) {
+                        if (k < nz) {
+                            typename Wide<VT>::T w4[4];
+                            Pack4<VT>::ld(v + k, w4);
+                            acc[k] += (AT)w4[0] * ur;
+                            acc[k + 1] += (AT)w4[1] * ur;
+                            acc[k + 2] += (AT)w4[2] * ur;
+                            acc[k + 3] += (AT)w4[3] * ur;
+                        }
+                    }
                 } else {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (t < nk) acc[t] += (AT)widen(vb[(int64_t)q * nz + t]) * ur;
+                    for (int k = 0; k < BNZ; ++k)
+                        if (k < nz) acc[k] += (AT)widen(v[k]) * ur;
                 }
             }
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], 16);
-            if (half == 0 && upd) {
-                const AT wsm = (AT)S.w;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    if (t < nk) {
-                        const int64_t jc = (int64_t)h * nz + k0 + t;
-                        const AT sv = acc[t] + wsm * laplace_strided<AT, ST>(S.U + S.m * R, jc, R, j,
-                                                                             S.nx, S.ny, nz);
-                        ST *vp = S.V + jc * R + j;
-                        const AT v = init ? sv * ib : sv * ib - cv * *vp;
-                        *vp = v;
-                        ss += (double)v * (double)v;
+            for (int k = 0; k < BNZ; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], 16);
+            const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+            bool finish = true;
+            if (nch > 1) {
+                ST *cp = S.chunk_part;
+                if (half == 0 && j < R)
+                    for (int k = 0; k < nz; ++k) cp[(li * nz + k) * RMAX + j] = acc[k];
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    const unsigned prev = atomicAdd(S.cell_done + h, 1u);
+                    last_flag[warp] = prev == (unsigned)(nch - 1);
+                }
+                __syncwarp();
+                finish = last_flag[warp] != 0;
+                if (finish) {
+                    __threadfence();
+                    const int64_t first = li - q0 / ADJ_CHUNK;
+                    for (int k = 0; k < nz; ++k) {
+                        AT sum = 0;
+                        for (int cch = 0; cch < nch; ++cch)
+                            sum += (AT)__ldcg(cp + ((first + cch) * nz + k) * RMAX + jj);
+                        acc[k] = sum;
                     }
+                    if (lane == 0) S.cell_done[h] = 0u;
+                }
+            }
+            if (finish && half == 0 && upd) {
+                const AT wsm = (AT)S.w;
+                for (int k = 0; k < nz; ++k) {
+                    const int64_t jc = (int64_t)h * nz + k;
+                    const AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * R, jc, R, j,
+                                                                         S.nx, S.ny, nz);
+                    ST *vp = S.V + (int64_t)j * S.n + jc;
+                    const AT v = init ? sv * ib : sv * ib - cv * *vp;
+                    *vp = v;
+                    ss += (double)v * (double)v;
                 }
             }
         }
@@ -292,7 +369,7 @@ __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const 
                 const int64_t c0 = li * LCOLS, c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 for (int64_t c = c0 + half; c < c1; c += 2) {
                     const int64_t i = c * S.R + j;
-                    const double v = (double)S.V[i] * ia;
+                    const double v = (double)S.V[(int64_t)j * S.n + c] * ia;
                     double w = S.W[i];
                     if (pend == 2) {
                         w = v;
@@ -310,22 +387,30 @@ __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const 
     }
 }
 
-// One block per system, one thread per right-hand side: sum the phase's
-// per-item partials in item order and advance that pair's scalars; thread 0
-// then counts the pairs still iterating.
+// One block of 256 threads per system: thread (l, j) sums the partials of items
+// l, l + 16, ... for right-hand side j, then thread j adds the 16 sums in
+// order (deterministic) and advances that pair's scalars; thread 0 finally
+// counts the pairs still iterating.
+constexpr int RED_T = 256;
+
 template <class VT, class ST>
-__global__ void k_bred(BSys<VT, ST> *sys, const int64_t *beg, const double *partial, int phase,
-                       int *active_out) {
-    const int s = blockIdx.x, j = threadIdx.x;
+__global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, const int64_t *beg,
+                                                const double *partial, int phase, int *active_out) {
+    __shared__ double part[RED_T / RMAX][RMAX];
+    const int s = blockIdx.x, t = threadIdx.x, j = t % RMAX, l = t / RMAX;
     BSys<VT, ST> &S = sys[s];
-    if (j < S.R) {
+    double acc = 0.0;
+    for (int64_t i = beg[s] + l; i < beg[s + 1]; i += RED_T / RMAX) acc += partial[i * RMAX + j];
+    part[l][j] = acc;
+    __syncthreads();
+    if (t < RMAX && j < S.R) {
         LsqrScalars *sc = S.sc + j;
         const bool frozen = (phase == PH_UPD) ? !sc->pending : (sc->done | sc->istop) != 0;
         if (!frozen) {
-            double t = 0.0;
-            for (int64_t i = beg[s]; i < beg[s + 1]; ++i) t += partial[i * RMAX + j];
+            double tsum = 0.0;
+            for (int k = 0; k < RED_T / RMAX; ++k) tsum += part[k][j];
             if (phase == PH_INIT) {
-                const double b = sqrt(t);
+                const double b = sqrt(tsum);
                 sc->beta = b;
                 sc->bnorm = b;
                 sc->rnorm = b;
@@ -333,14 +418,14 @@ __global__ void k_bred(BSys<VT, ST> *sys, const int64_t *beg, const double *part
                 if (!isfinite(b)) sc->err = 1;
                 if (!(b > 0.0) || !isfinite(b)) sc->done = 1;
             } else if (phase == PH_FWD) {
-                const double b = sqrt(t);
+                const double b = sqrt(tsum);
                 if (!isfinite(b)) {
                     sc->err = 1;
                     sc->done = 1;
                 }
                 sc->beta = b;
             } else if (phase == PH_ADJ_INIT || phase == PH_ADJ) {
-                const double an = (phase == PH_ADJ && !(sc->beta > 0.0)) ? sc->alpha : sqrt(t);
+                const double an = (phase == PH_ADJ && !(sc->beta > 0.0)) ? sc->alpha : sqrt(tsum);
                 if (!isfinite(an)) {
                     sc->err = 1;
                     sc->done = 1;
@@ -354,13 +439,13 @@ __global__ void k_bred(BSys<VT, ST> *sys, const int64_t *beg, const double *part
                     lsqr_step(sc, an);
                 }
             } else {
-                sc->wnorm2 = t;
+                sc->wnorm2 = tsum;
                 sc->pending = 0;
             }
         }
     }
     __syncthreads();
-    if (j == 0) {
+    if (t == 0) {
         int a = 0;
         for (int k = 0; k < S.R; ++k) a += !(S.sc[k].done | S.sc[k].istop);
         S.active = a;
@@ -438,8 +523,7 @@ template <class VT, class ST> struct Batched {
         bw->hu.assign(nsys + 1, 0);
         for (int i = 0; i < nsys; ++i) {
             pdst_handle *h = hs[i];
-            const int kg = (h->nz + 3) / 4;
-            bw->ha[i + 1] = bw->ha[i] + (int64_t)h->H * kg;
+            bw->ha[i + 1] = bw->ha[i] + h->n_adj;
             bw->hu[i + 1] = bw->hu[i] + ((int64_t)h->n + LCOLS - 1) / LCOLS;
         }
         bw->nf_items = bw->hf[nsys];
@@ -452,7 +536,11 @@ template <class VT, class ST> struct Batched {
                 pdst_handle *h = hs[i];
                 const int R = nrhs[i];
                 DevBuf *U = new DevBuf, *V = new DevBuf, *X = new DevBuf, *W = new DevBuf;
-                bw->bufs.insert(bw->bufs.end(), {U, V, X, W});
+                DevBuf *CP = new DevBuf, *CD = new DevBuf;
+                bw->bufs.insert(bw->bufs.end(), {U, V, X, W, CP, CD});
+                PDST_TRY(CP->alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz * RMAX, 1)));
+                PDST_TRY(CD->alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
+                PDST_CUDA(cudaMemsetAsync(CD->p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
                 PDST_TRY(U->alloc(sizeof(ST) * (h->m + h->n) * R));
                 PDST_TRY(V->alloc(sizeof(ST) * (int64_t)h->n * R));
                 PDST_TRY(X->alloc(sizeof(double) * (int64_t)h->n * R));
@@ -486,10 +574,13 @@ template <class VT, class ST> struct Batched {
             q.cell_rows = h->cell_rows.as<int32_t>();
             q.cell_order = h->cell_order.as<int32_t>();
             q.valB = h->vals[dtype].bcsc.as<VT>();
-            q.U = bw->bufs[4 * i]->as<ST>();
-            q.V = bw->bufs[4 * i + 1]->as<ST>();
-            q.X = bw->bufs[4 * i + 2]->as<double>();
-            q.W = bw->bufs[4 * i + 3]->as<double>();
+            q.U = bw->bufs[NB * i]->as<ST>();
+            q.V = bw->bufs[NB * i + 1]->as<ST>();
+            q.X = bw->bufs[NB * i + 2]->as<double>();
+            q.W = bw->bufs[NB * i + 3]->as<double>();
+            q.chunk_part = bw->bufs[NB * i + 4]->as<ST>();
+            q.cell_done = bw->bufs[NB * i + 5]->as<unsigned>();
+            q.adj_item = h->adj_item.as<int32_t>();
             q.sc = scd + (size_t)i * RMAX;
             q.nf = nf[i];
             q.active = 0;
@@ -518,6 +609,8 @@ template <class VT, class ST> struct Batched {
             d[i].active = d[i].R;
         }
         PDST_CUDA(cudaMemcpyAsync(bw->desc.p, d.data(), sizeof(Sys) * nsys, cudaMemcpyHostToDevice, s));
+        for (int i = 0; i < nsys; ++i)
+            PDST_CUDA(cudaMemsetAsync(bw->bufs[NB * i + 5]->p, 0, bw->bufs[NB * i + 5]->bytes, s));
         std::copy(init.begin(), init.end(), bw->h_scal);
         PDST_CUDA(cudaMemcpyAsync(bw->scal.p, bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX,
                                   cudaMemcpyHostToDevice, s));
@@ -530,15 +623,15 @@ template <class VT, class ST> struct Batched {
         double *part = bw->partial.as<double>();
         k_bfwd<VT, ST><<<bgrid(k_bfwd<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
             sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_FWD,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_FWD,
                                            bw->active.as<int>());
         k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
             sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ,
                                            bw->active.as<int>());
         k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
             sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
                                            bw->active.as<int>());
     }
 
@@ -547,21 +640,22 @@ template <class VT, class ST> struct Batched {
         double *part = bw->partial.as<double>();
         k_binit<VT, ST><<<bgrid(k_binit<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
             sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_INIT,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_INIT,
                                            bw->active.as<int>());
         k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
             sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ_INIT,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ_INIT,
                                            bw->active.as<int>());
         k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
             sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, 32, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
                                            bw->active.as<int>());
         PDST_CUDA(cudaGetLastError());
         return PDST_OK;
     }
 
-    // Time the forward phase for each candidate tile and keep the fastest.
+    // Time one whole iteration for each candidate tile and keep the fastest
+    // (the start-up phase runs first, so the iterations do real work).
     static pdst_status autotune(BatchWork *bw, const std::vector<pdst_handle *> &hs,
                                 const int32_t *nrhs, int dtype, const double *const *d_dev,
                                 const std::vector<LsqrScalars> &init, int device, cudaStream_t s) {
@@ -579,11 +673,10 @@ template <class VT, class ST> struct Batched {
             PDST_TRY(start(bw, nsys, device, s));
             Sys *sys = bw->desc.as<Sys>();
             float ms = 0.f, tot = 0.f;
+            (void)sys;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
-                k_bfwd<VT, ST><<<bgrid(k_bfwd<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
-                    sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
-                    bw->partial.as<double>());
+                launch_iter(bw, nsys, device, s);
                 cudaEventRecord(e1, s);
                 PDST_CUDA(cudaEventSynchronize(e1));
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -657,7 +750,7 @@ template <class VT, class ST> struct Batched {
             launches += 6 * kblock;
         }
         for (int i = 0; i < nsys; ++i)
-            PDST_CUDA(cudaMemcpyAsync(m_out[i], bw->bufs[4 * i + 2]->p,
+            PDST_CUDA(cudaMemcpyAsync(m_out[i], bw->bufs[NB * i + 2]->p,
                                       sizeof(double) * (int64_t)hs[i]->n * nrhs[i],
                                       cudaMemcpyDeviceToDevice, s));
         PDST_CUDA(cudaMemcpyAsync(bw->h_scal, bw->scal.p, sizeof(LsqrScalars) * nsys * RMAX,
@@ -708,6 +801,11 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
         if (!hs[i]->vals[dtype].present) {
             set_error("pdst_lsqr_batched: values of dtype %d were not kept in handle %d", dtype, i);
             return PDST_ERR_STATE;
+        }
+        if (hs[i]->nz > BNZ) {
+            set_error("pdst_lsqr_batched: nz = %d in handle %d; the batched form supports nz <= %d",
+                      hs[i]->nz, i, BNZ);
+            return PDST_ERR_LIMIT;
         }
         H[i] = hs[i];
     }
