@@ -36,6 +36,8 @@ constexpr int NB = 6;        // work buffers per system: U, V, X, W, chunk sums,
 template <class VT, class ST> struct BSys {
     int64_t m;
     int32_t n, nx, ny, nz, R;
+    int32_t RS;       // row stride of V: R rounded up to 4, 8 or 16
+    int64_t n_adj;    // adjoint work items
     double w;
     const int64_t *row_cptr;
     const int32_t *row_cells;
@@ -48,8 +50,8 @@ template <class VT, class ST> struct BSys {
     const int32_t *adj_item;   // (cell, first row) per adjoint work item
     ST *chunk_part;   // adjoint work items x nz x RMAX partial sums
     unsigned *cell_done;       // H finished-chunk counters
-    ST *U;            // (m + n) x R, right-hand side fastest
-    ST *V;            // R x n, right-hand side major
+    ST *U;            // (m + n) x RS, right-hand side fastest (padding lanes stay 0)
+    ST *V;            // n x RS, right-hand side fastest (padding lanes stay 0)
     double *X, *W;    // n x R
     const double *d;  // m x R
     LsqrScalars *sc;  // R
@@ -59,6 +61,8 @@ template <class VT, class ST> struct BSys {
 
 enum { PH_INIT = 0, PH_FWD = 1, PH_ADJ_INIT = 2, PH_ADJ = 3, PH_UPD = 4 };
 
+constexpr int WPB = BT / 32;   // warps per block
+
 __device__ __forceinline__ int find_sys(const int64_t *__restrict__ beg, int nsys, int64_t it) {
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
@@ -67,6 +71,36 @@ __device__ __forceinline__ int find_sys(const int64_t *__restrict__ beg, int nsy
     }
     return lo;
 }
+
+// Per-warp running sums of the per-pair partials.  Warp g (of NW = gridDim.x *
+// WPB) takes warp items g, g + NW, ...; lane j (< RMAX, both half-warps already
+// added) keeps the running sum of right-hand side j for the current system and
+// writes it to slot (system, g) of `partial` when the warp moves on to a later
+// system (systems skipped get 0).  Which items a warp takes, and so the order
+// of every sum, depends only on the grid, so the totals are bit-reproducible
+// for a given launch shape; no block-wide barrier is needed.
+struct WarpSum {
+    double run = 0.0;
+    int cur = 0;
+    __device__ __forceinline__ void put(double *partial, int sys, int64_t g, int64_t nw,
+                                        double v) const {
+        const int lane = threadIdx.x & 31;
+        if (lane < RMAX) partial[((int64_t)sys * nw + g) * RMAX + lane] = v;
+    }
+    __device__ __forceinline__ void add(double ss, int s, double *partial, int64_t g, int64_t nw) {
+        if (s != cur) {
+            put(partial, cur, g, nw, run);
+            for (int q = cur + 1; q < s; ++q) put(partial, q, g, nw, 0.0);
+            run = 0.0;
+            cur = s;
+        }
+        run += ss;
+    }
+    __device__ __forceinline__ void finish(double *partial, int nsys, int64_t g, int64_t nw) const {
+        put(partial, cur, g, nw, run);
+        for (int q = cur + 1; q < nsys; ++q) put(partial, q, g, nw, 0.0);
+    }
+};
 
 // Per-lane column state: lane j of each half-warp owns right-hand side j.
 struct Col {
@@ -108,6 +142,7 @@ __device__ __forceinline__ AT laplace_strided(const ST *__restrict__ x, int64_t 
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                               int64_t nitems, int TR, double *partial) {
+    WarpSum ws;
     const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -122,40 +157,146 @@ __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const
                 const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
                 for (int64_t r = r0 + half; r < r1; r += 2) {
                     const double v = S.d[r * R + j];
-                    S.U[r * R + j] = (ST)v;
+                    S.U[r * S.RS + j] = (ST)v;
                     ss += v * v;
                 }
             } else {
                 const int64_t c0 = (li - S.nf) * LCOLS;
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 for (int64_t c = c0 + half; c < c1; c += 2) {
-                    S.U[(S.m + c) * R + j] = (ST)0;
-                    S.V[(int64_t)j * S.n + c] = (ST)0;
+                    S.U[(S.m + c) * S.RS + j] = (ST)0;
+                    S.V[c * S.RS + j] = (ST)0;
                     S.X[c * R + j] = 0.0;
                     S.W[c * R + j] = 0.0;
                 }
             }
         }
         ss += __shfl_xor_sync(FULL, ss, 16);
-        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+        ws.add(ss, s, partial, gw, nw);
+    }
+    ws.finish(partial, nsys, gw, nw);
+}
+
+__device__ __forceinline__ int pick4(const int cc[4], int ci) {
+    return ci == 0 ? cc[0] : ci == 1 ? cc[1] : ci == 2 ? cc[2] : cc[3];
+}
+
+// The G rows of one forward work item (half-warp per row; lane j of each half
+// ends with right-hand side j's (G v)_r).  V is stored right-hand side fastest
+// with a row stride RS of 4, 8 or 16, so a run's block of V (nz depths x RS
+// right-hand sides, contiguous) is read as 16-byte vectors: lane t of a
+// half-warp takes the group g = t mod (RS/4) of four right-hand sides at
+// depths t div (RS/4), + 16/(RS/4), ..., and each of its loads meets the other
+// lanes' in one contiguous 256-byte span.  The run's value at that depth is
+// loaded by the RS/4 lanes that share it.  At the row end the lanes of one
+// group are summed by shuffles (fixed order) and lane j takes right-hand side
+// j.  The row's first 64 cells are read into registers once and broadcast by
+// shuffle.  NZC > 0 (with RS = 16) fixes nz at compile time: each lane's
+// depths unroll and two runs are loaded before their products are summed.
+template <int NZC, class VT, class ST>
+__device__ __forceinline__ void fwd_g_item(const BSys<VT, ST> &S, int64_t li, int TR, const Col &c,
+                                           ST ia, ST cu, int j, int half, double &ss) {
+    using AT = ST;
+    const int R = S.R, RS = NZC ? 16 : S.RS, nz = NZC ? NZC : S.nz;
+    const int G4 = RS >> 2, lg = G4 >> 1;   // groups of 4; log2(G4)
+    const int g = j & (G4 - 1), k0 = j >> lg, kst = 16 >> lg;
+    const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
+    // both halves iterate the same number of times (shuffles below)
+    const int64_t nrows = (r1 - r0 + 1) / 2;
+    for (int64_t t = 0; t < nrows; ++t) {
+        const int64_t r = r0 + 2 * t + half;
+        const bool live = r < r1;
+        int64_t e0 = 0, e1 = 0;
+        if (live) {
+            e0 = __ldg(S.row_cptr + r);
+            e1 = __ldg(S.row_cptr + r + 1);
+        }
+        const int nrun = (int)(e1 - e0);
+        int cc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            cc[i] = (j + 16 * i < nrun) ? __ldg(S.row_cells + e0 + j + 16 * i) : 0;
+        // the two halves may have different run counts: loop to the max
+        int nmax = nrun;
+        nmax = max(nmax, __shfl_xor_sync(FULL, nmax, 16));
+        AT a4[4] = {0, 0, 0, 0};
+        if constexpr (NZC > 0) {
+            constexpr int NI = NZC / 4;   // depths per lane (k0, k0 + 4, ...)
+            const VT *vrow = S.val + e0 * NZC + k0;
+            const ST *vb = S.V + 4 * g + k0 * 16;
+            for (int e = 0; e < nmax; e += 2) {
+                const int h0 = __shfl_sync(FULL, pick4(cc, e >> 4), (half << 4) | (e & 15));
+                const int h1 =
+                    __shfl_sync(FULL, pick4(cc, (e + 1) >> 4), (half << 4) | ((e + 1) & 15));
+                if (e >= nrun) continue;
+                const bool two = e + 1 < nrun;
+                const int c0 = e < 64 ? h0 : __ldg(S.row_cells + e0 + e);
+                const int c1 = !two ? c0 : (e + 1 < 64 ? h1 : __ldg(S.row_cells + e0 + e + 1));
+                AT va[2][NI];
+                ST xv[2][NI][4];
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    va[0][i] = (AT)ldval(vrow + (int64_t)e * NZC + 4 * i);
+                    ldx4<ST>(vb + (int64_t)c0 * (NZC * 16) + 64 * i, xv[0][i]);
+                }
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    va[1][i] = two ? (AT)ldval(vrow + (int64_t)(e + 1) * NZC + 4 * i) : (AT)0;
+                    ldx4<ST>(vb + (int64_t)c1 * (NZC * 16) + 64 * i, xv[1][i]);
+                }
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) a4[q] += va[0][i] * (AT)xv[0][i][q];
+                if (two) {
+#pragma unroll
+                    for (int i = 0; i < NI; ++i)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) a4[q] += va[1][i] * (AT)xv[1][i][q];
+                }
+            }
+        } else {
+            for (int e = 0; e < nmax; ++e) {
+                int h = __shfl_sync(FULL, pick4(cc, e >> 4), (half << 4) | (e & 15));
+                if (e >= nrun) continue;
+                if (e >= 64) h = __ldg(S.row_cells + e0 + e);
+                const VT *v = S.val + (e0 + e) * nz;
+                const ST *xb = S.V + (int64_t)h * nz * RS + 4 * g;
+                for (int k = k0; k < nz; k += kst) {
+                    const AT a = (AT)ldval(v + k);
+                    ST xv[4];
+                    ldx4<ST>(xb + (int64_t)k * RS, xv);
+                    a4[0] += a * (AT)xv[0];
+                    a4[1] += a * (AT)xv[1];
+                    a4[2] += a * (AT)xv[2];
+                    a4[3] += a * (AT)xv[3];
+                }
+            }
+        }
+        for (int off = G4; off < 16; off <<= 1)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a4[i] += __shfl_xor_sync(FULL, a4[i], off);
+        // lane j takes component j mod 4 of group j div 4 (held by lane j div 4)
+        const int sl = (half << 4) | (j >> 2);
+        AT q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = __shfl_sync(FULL, a4[i], sl);
+        const int cpt = j & 3;
+        const AT acc = cpt == 0 ? q[0] : cpt == 1 ? q[1] : cpt == 2 ? q[2] : q[3];
+        if (live && c.act) {
+            const AT u = acc * ia - cu * S.U[r * RS + j];
+            S.U[r * RS + j] = u;
+            ss += (double)u * (double)u;
+        }
     }
 }
 
-// Laplacian of column jc of one right-hand side stored contiguously (x[c]).
-template <class AT, class ST>
-__device__ __forceinline__ AT laplace_col(const ST *__restrict__ x, int64_t jc, int nx, int ny,
-                                          int nz) {
-    return laplace<AT, ST>(x, jc, nx, ny, nz);
-}
-
-// Forward phase: G rows (half-warp per row, lane j = right-hand side j; V is
-// stored right-hand-side major, so each lane reads its column's nz entries of
-// a run as nz/4 16-byte vectors; the row's first 64 cells are read into
-// registers once and broadcast by shuffle) and the w L rows (column tiles).
+// Forward phase: G rows (fwd_g_item) and the w L rows (column tiles).
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int TR, double *partial) {
     using AT = ST;
+    WarpSum ws;
     const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -165,69 +306,26 @@ __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const 
         const int64_t li = it - beg[s];
         double ss = 0.0;
         if (S.active > 0) {
-            const int R = S.R, nz = S.nz;
+            const int R = S.R, RS = S.RS, nz = S.nz;
             const int jj = j < R ? j : 0;
             const Col c = col_state(S.sc, j, R);
             const AT ia = c.alpha > 0.0 ? (AT)(1.0 / c.alpha) : (AT)0;
             const AT cu = c.beta > 0.0 ? (AT)(c.alpha / c.beta) : (AT)0;
-            const ST *Vj = S.V + (int64_t)jj * S.n;
             if (li < S.nf) {
-                const int64_t r0 = li * TR, r1 = r0 + TR < S.m ? r0 + TR : S.m;
-                // both halves iterate the same number of times (shuffles below)
-                const int64_t nrows = (r1 - r0 + 1) / 2;
-                for (int64_t t = 0; t < nrows; ++t) {
-                    const int64_t r = r0 + 2 * t + half;
-                    const bool live = r < r1;
-                    int64_t e0 = 0, e1 = 0;
-                    if (live) {
-                        e0 = __ldg(S.row_cptr + r);
-                        e1 = __ldg(S.row_cptr + r + 1);
-                    }
-                    const int nrun = (int)(e1 - e0);
-                    int cc[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        cc[i] = (j + 16 * i < nrun) ? __ldg(S.row_cells + e0 + j + 16 * i) : 0;
-                    // the two halves may have different run counts: loop to the max
-                    int nmax = nrun;
-                    nmax = max(nmax, __shfl_xor_sync(FULL, nmax, 16));
-                    AT acc = 0;
-                    for (int e = 0; e < nmax; ++e) {
-                        const int src = (half << 4) | (e & 15);
-                        const int ci = e >> 4;
-                        int h = __shfl_sync(FULL, ci == 0 ? cc[0] : ci == 1 ? cc[1]
-                                                        : ci == 2 ? cc[2] : cc[3], src);
-                        if (e >= nrun) continue;
-                        if (e >= 64) h = __ldg(S.row_cells + e0 + e);
-                        const VT *v = S.val + (e0 + e) * nz;
-                        const ST *xb = Vj + (int64_t)h * nz;
-                        if ((nz & 3) == 0) {
-                            for (int k = 0; k < nz; k += 4) {
-                                typename Wide<VT>::T q[4];
-                                ST xv[4];
-                                Pack4<VT>::ld(v + k, q);
-                                ldx4<ST>(xb + k, xv);
-                                acc += (AT)q[0] * (AT)xv[0] + (AT)q[1] * (AT)xv[1] +
-                                       (AT)q[2] * (AT)xv[2] + (AT)q[3] * (AT)xv[3];
-                            }
-                        } else {
-                            for (int k = 0; k < nz; ++k) acc += (AT)widen(v[k]) * (AT)xb[k];
-                        }
-                    }
-                    if (live && c.act) {
-                        const AT u = acc * ia - cu * S.U[r * R + j];
-                        S.U[r * R + j] = u;
-                        ss += (double)u * (double)u;
-                    }
-                }
+                if (RS == 16 && nz == 16)
+                    fwd_g_item<16>(S, li, TR, c, ia, cu, j, half, ss);
+                else if (RS == 16 && nz == 8)
+                    fwd_g_item<8>(S, li, TR, c, ia, cu, j, half, ss);
+                else
+                    fwd_g_item<0>(S, li, TR, c, ia, cu, j, half, ss);
             } else {
                 const int64_t c0 = (li - S.nf) * LCOLS;
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 const AT wsm = (AT)S.w;
                 for (int64_t jc = c0 + half; jc < c1; jc += 2) {
-                    const AT lap = laplace_col<AT, ST>(Vj, jc, S.nx, S.ny, nz);
+                    const AT lap = laplace_strided<AT, ST>(S.V, jc, RS, jj, S.nx, S.ny, nz);
                     if (c.act) {
-                        ST *up = S.U + (S.m + jc) * R + j;
+                        ST *up = S.U + (S.m + jc) * RS + j;
                         const AT u = wsm * lap * ia - cu * *up;
                         *up = u;
                         ss += (double)u * (double)u;
@@ -236,122 +334,313 @@ __global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const 
             }
         }
         ss += __shfl_xor_sync(FULL, ss, 16);
-        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+        ws.add(ss, s, partial, gw, nw);
     }
+    ws.finish(partial, nsys, gw, nw);
 }
 
 constexpr int BNZ = 16;   // depths per cell handled in registers by the adjoint
 
+// Laplacian of column jc for right-hand sides 4g..4g+3 of a block stored with
+// row stride 16 (same neighbour order as laplace_strided).
+template <class AT, class ST>
+__device__ __forceinline__ void laplace4(const ST *__restrict__ x, int64_t jc, int g, int nx, int ny,
+                                         int nz, AT out[4]) {
+    const int k = (int)(jc % nz);
+    const int64_t hh = jc / nz;
+    const int ix = (int)(hh % nx), iy = (int)(hh / nx);
+    const int64_t sy = (int64_t)nx * nz;
+    const ST *p = x + jc * 16 + 4 * g;
+    ST c[4];
+    ldx4<ST>(p, c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = 0;
+    auto nb = [&](int64_t o) {
+        ST t[4];
+        ldx4<ST>(p + o * 16, t);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] += (AT)c[q] - (AT)t[q];
+    };
+    if (k > 0) nb(-1);
+    if (k < nz - 1) nb(1);
+    if (ix > 0) nb(-nz);
+    if (ix < nx - 1) nb(nz);
+    if (iy > 0) nb(-sy);
+    if (iy < ny - 1) nb(sy);
+}
+
+// Chunk bookkeeping shared by both adjoint paths: store this chunk's sums,
+// count the finished chunks of the cell, and tell whether this warp holds the
+// cell's last chunk (which then sums all chunks in chunk order).
+__device__ __forceinline__ bool adj_last_chunk(unsigned *cell_done, int h, int nch, int lane,
+                                               int *flag) {
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned prev = atomicAdd(cell_done + h, 1u);
+        *flag = prev == (unsigned)(nch - 1);
+    }
+    __syncwarp();
+    const bool last = *flag != 0;
+    if (last) {
+        __threadfence();
+        if (lane == 0) cell_done[h] = 0u;
+    }
+    return last;
+}
+
+// Adjoint work item with RS = 16 and nz = NZC (8 or 16): NZC lanes per row,
+// lane t of a row owning right-hand sides 4g..4g+3 (g = t mod 4) at depths
+// 4kq..4kq+3 (kq = t div 4); a row's u block (64 bytes) and nz values are
+// read as 16-byte vectors and each lane does a 4 x 4 outer product.  The
+// 32 / NZC row slots of the warp take rows q, q + 32/NZC, ... (two per step)
+// and are summed by shuffles (fixed order).  Lanes 0..15 return the sum of
+// squares of the new v for right-hand side = lane.
+template <int NZC, class VT, class ST>
+__device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, int init, int lane,
+                                             int *flag) {
+    using AT = ST;
+    using WT = typename Wide<VT>::T;
+    constexpr int LPR = NZC, RPW = 32 / LPR;
+    const int sub = lane / LPR, t = lane % LPR, g = t & 3, kq = t >> 2;
+    const int h = __ldg(S.adj_item + 2 * li);
+    const int q0 = __ldg(S.adj_item + 2 * li + 1);
+    const int64_t c0 = __ldg(S.cell_rptr + h);
+    const int cnt = __ldg(S.cell_cnt + h);
+    const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
+    const int32_t *rows = S.cell_rows + c0;
+    const VT *vb = S.valB + c0 * NZC + 4 * kq;
+    const ST *ub = S.U + 4 * g;
+    AT acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    int ra = q0 + sub < q1 ? __ldg(rows + q0 + sub) : 0;
+    int rb = q0 + sub + RPW < q1 ? __ldg(rows + q0 + sub + RPW) : 0;
+    for (int q = q0 + sub; q < q1; q += 2 * RPW) {
+        const bool two = q + RPW < q1;
+        const int na = q + 2 * RPW < q1 ? __ldg(rows + q + 2 * RPW) : 0;
+        const int nb = q + 3 * RPW < q1 ? __ldg(rows + q + 3 * RPW) : 0;
+        ST u0[4], u1[4] = {0, 0, 0, 0};
+        WT w0[4], w1[4] = {0, 0, 0, 0};
+        ldx4<ST>(ub + (int64_t)ra * 16, u0);
+        Pack4<VT>::ld(vb + (int64_t)q * NZC, w0);
+        if (two) {
+            ldx4<ST>(ub + (int64_t)rb * 16, u1);
+            Pack4<VT>::ld(vb + (int64_t)(q + RPW) * NZC, w1);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += (AT)w0[a] * (AT)u0[b];
+        if (two) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += (AT)w1[a] * (AT)u1[b];
+        }
+        ra = na;
+        rb = nb;
+    }
+    for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += __shfl_xor_sync(FULL, acc[a][b], off);
+    const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+    bool finish = true;
+    if (nch > 1) {
+        ST *cp = S.chunk_part;
+        if (sub == 0)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    cp[(li * NZC + 4 * kq + a) * RMAX + 4 * g + b] = acc[a][b];
+        finish = adj_last_chunk(S.cell_done, h, nch, lane, flag);
+        if (finish) {
+            const int64_t first = li - q0 / ADJ_CHUNK;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    AT sum = 0;
+                    for (int cch = 0; cch < nch; ++cch)
+                        sum += (AT)__ldcg(cp + ((first + cch) * NZC + 4 * kq + a) * RMAX + 4 * g + b);
+                    acc[a][b] = sum;
+                }
+        }
+    }
+    double ss4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (finish && sub == 0) {
+        bool upd[4];
+        AT ib[4], cv[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const Col c = col_state(S.sc, 4 * g + b, S.R);
+            upd[b] = c.act && (init || c.beta > 0.0);
+            ib[b] = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
+            cv[b] = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
+        }
+        const AT wsm = (AT)S.w;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t jc = (int64_t)h * NZC + 4 * kq + a;
+            AT lap[4];
+            laplace4<AT, ST>(S.U + S.m * 16, jc, g, S.nx, S.ny, NZC, lap);
+            ST *vp = S.V + jc * 16 + 4 * g;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (!upd[b]) continue;
+                const AT sv = acc[a][b] + wsm * lap[b];
+                const AT v = init ? sv * ib[b] : sv * ib[b] - cv[b] * vp[b];
+                vp[b] = v;
+                ss4[b] += (double)v * (double)v;
+            }
+        }
+    }
+    // per right-hand side: lanes with equal g (xor 4, 8, 16), then lane j takes j
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        ss4[b] += __shfl_xor_sync(FULL, ss4[b], 4);
+        ss4[b] += __shfl_xor_sync(FULL, ss4[b], 8);
+        ss4[b] += __shfl_xor_sync(FULL, ss4[b], 16);
+    }
+    const int j = lane & 15;
+    double q[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) q[b] = __shfl_sync(FULL, ss4[b], j >> 2);
+    const int cpt = j & 3;
+    const double r = cpt == 0 ? q[0] : cpt == 1 ? q[1] : cpt == 2 ? q[2] : q[3];
+    return lane < 16 ? r : 0.0;
+}
+
+// Adjoint work item, any RS and nz <= BNZ: lane j = right-hand side j, the two
+// half-warps take alternate rows; each row's index and u are read once and its
+// nz values as nz/4 16-byte vectors (blocked CSC).  Lanes j of the first half
+// return the sum of squares of the new v for right-hand side j.
+template <class VT, class ST>
+__device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li, int init, int lane,
+                                               int *flag) {
+    using AT = ST;
+    const int j = lane & 15, half = lane >> 4;
+    const int R = S.R, RS = S.RS, nz = S.nz;
+    const int jj = j < R ? j : 0;
+    const Col c = col_state(S.sc, j, R);
+    const bool upd = c.act && (init || c.beta > 0.0);
+    const AT ib = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
+    const AT cv = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
+    const int h = __ldg(S.adj_item + 2 * li);
+    const int q0 = __ldg(S.adj_item + 2 * li + 1);
+    const int64_t c0 = __ldg(S.cell_rptr + h);
+    const int cnt = __ldg(S.cell_cnt + h);
+    const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
+    const int32_t *rows = S.cell_rows + c0;
+    const VT *vb = S.valB + c0 * nz;
+    AT acc[BNZ];
+#pragma unroll
+    for (int k = 0; k < BNZ; ++k) acc[k] = 0;
+    int rnext = (q0 + half < q1) ? __ldg(rows + q0 + half) : -1;
+    for (int q = q0 + half; q < q1; q += 2) {
+        const int r = rnext;
+        rnext = (q + 2 < q1) ? __ldg(rows + q + 2) : -1;
+        const AT ur = (AT)S.U[(int64_t)r * RS + jj];
+        const VT *v = vb + (int64_t)q * nz;
+        if ((nz & 3) == 0) {
+#pragma unroll
+            for (int k = 0; k < BNZ; k += 4) {
+                if (k < nz) {
+                    typename Wide<VT>::T w4[4];
+                    Pack4<VT>::ld(v + k, w4);
+                    acc[k] += (AT)w4[0] * ur;
+                    acc[k + 1] += (AT)w4[1] * ur;
+                    acc[k + 2] += (AT)w4[2] * ur;
+                    acc[k + 3] += (AT)w4[3] * ur;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k)
+                if (k < nz) acc[k] += (AT)widen(v[k]) * ur;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < BNZ; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], 16);
+    const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+    bool finish = true;
+    if (nch > 1) {
+        ST *cp = S.chunk_part;
+        if (half == 0 && j < R)
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k)
+                if (k < nz) cp[(li * nz + k) * RMAX + j] = acc[k];
+        finish = adj_last_chunk(S.cell_done, h, nch, lane, flag);
+        if (finish) {
+            const int64_t first = li - q0 / ADJ_CHUNK;
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k) {
+                if (k >= nz) continue;
+                AT sum = 0;
+                for (int cch = 0; cch < nch; ++cch)
+                    sum += (AT)__ldcg(cp + ((first + cch) * nz + k) * RMAX + jj);
+                acc[k] = sum;
+            }
+        }
+    }
+    double ss = 0.0;
+    if (finish && half == 0 && upd) {
+        const AT wsm = (AT)S.w;
+#pragma unroll
+        for (int k = 0; k < BNZ; ++k) {
+            if (k >= nz) continue;
+            const int64_t jc = (int64_t)h * nz + k;
+            const AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * RS, jc, RS, j, S.nx,
+                                                                 S.ny, nz);
+            ST *vp = S.V + jc * RS + j;
+            const AT v = init ? sv * ib : sv * ib - cv * *vp;
+            *vp = v;
+            ss += (double)v * (double)v;
+        }
+    }
+    return ss;
+}
+
 // Adjoint phase: work item = a chunk of up to ADJ_CHUNK rows of one cell of
-// one system (the handle's adjoint work list).  Lane j = right-hand side j;
-// the two half-warps take alternate rows; each row's index and u are read
-// once and its nz values as nz/4 16-byte vectors (blocked CSC).  A cell split
-// over several chunks is finished by its last chunk (chunk order sums).
+// one system (the handle's adjoint work list).  A cell split over several
+// chunks is finished by its last chunk (chunk order sums).
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int init, double *partial) {
-    using AT = ST;
-    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    __shared__ int last_flag[WPB];
+    WarpSum ws;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    __shared__ int last_flag[BT / 32];
-    const int warp = threadIdx.x >> 5;
     for (int64_t it = gw; it < nitems; it += nw) {
         const int s = find_sys(beg, nsys, it);
         const BSys<VT, ST> &S = sys[s];
         const int64_t li = it - beg[s];
         double ss = 0.0;
-        if (S.active > 0) {
-            const int R = S.R, nz = S.nz;
-            const int jj = j < R ? j : 0;
-            const Col c = col_state(S.sc, j, R);
-            const bool upd = c.act && (init || c.beta > 0.0);
-            const AT ib = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
-            const AT cv = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
-            const int h = __ldg(S.adj_item + 2 * li);
-            const int q0 = __ldg(S.adj_item + 2 * li + 1);
-            const int64_t c0 = __ldg(S.cell_rptr + h);
-            const int cnt = __ldg(S.cell_cnt + h);
-            const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
-            const int32_t *rows = S.cell_rows + c0;
-            const VT *vb = S.valB + c0 * nz;
-            AT acc[BNZ];
-#pragma unroll
-            for (int k = 0; k < BNZ; ++k) acc[k] = 0;
-            int rnext = (q0 + half < q1) ? __ldg(rows + q0 + half) : -1;
-            for (int q = q0 + half; q < q1; q += 2) {
-                const int r = rnext;
-                rnext = (q + 2 < q1) ? __ldg(rows + q + 2) : -1;
-                const AT ur = (AT)S.U[(int64_t)r * R + jj];
-                const VT *v = vb + (int64_t)q * nz;
-                if ((nz & 3) == 0) {
-#pragma unroll
-                    for (int k = 0; k < BNZ; k += 4) {
-                        if (k < nz) {
-                            typename Wide<VT>::T w4[4];
-                            Pack4<VT>::ld(v + k, w4);
-                            acc[k] += (AT)w4[0] * ur;
-                            acc[k + 1] += (AT)w4[1] * ur;
-                            acc[k + 2] += (AT)w4[2] * ur;
-                            acc[k + 3] += (AT)w4[3] * ur;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < BNZ; ++k)
-                        if (k < nz) acc[k] += (AT)widen(v[k]) * ur;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < BNZ; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], 16);
-            const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
-            bool finish = true;
-            if (nch > 1) {
-                ST *cp = S.chunk_part;
-                if (half == 0 && j < R)
-                    for (int k = 0; k < nz; ++k) cp[(li * nz + k) * RMAX + j] = acc[k];
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) {
-                    const unsigned prev = atomicAdd(S.cell_done + h, 1u);
-                    last_flag[warp] = prev == (unsigned)(nch - 1);
-                }
-                __syncwarp();
-                finish = last_flag[warp] != 0;
-                if (finish) {
-                    __threadfence();
-                    const int64_t first = li - q0 / ADJ_CHUNK;
-                    for (int k = 0; k < nz; ++k) {
-                        AT sum = 0;
-                        for (int cch = 0; cch < nch; ++cch)
-                            sum += (AT)__ldcg(cp + ((first + cch) * nz + k) * RMAX + jj);
-                        acc[k] = sum;
-                    }
-                    if (lane == 0) S.cell_done[h] = 0u;
-                }
-            }
-            if (finish && half == 0 && upd) {
-                const AT wsm = (AT)S.w;
-                for (int k = 0; k < nz; ++k) {
-                    const int64_t jc = (int64_t)h * nz + k;
-                    const AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * R, jc, R, j,
-                                                                         S.nx, S.ny, nz);
-                    ST *vp = S.V + (int64_t)j * S.n + jc;
-                    const AT v = init ? sv * ib : sv * ib - cv * *vp;
-                    *vp = v;
-                    ss += (double)v * (double)v;
-                }
-            }
+        if (S.active > 0 && li < S.n_adj) {
+            if (S.RS == 16 && S.nz == 16)
+                ss = adj_item16<16>(S, li, init, lane, last_flag + warp);
+            else if (S.RS == 16 && S.nz == 8)
+                ss = adj_item16<8>(S, li, init, lane, last_flag + warp);
+            else
+                ss = adj_item_any(S, li, init, lane, last_flag + warp);
         }
         ss += __shfl_xor_sync(FULL, ss, 16);
-        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+        ws.add(ss, s, partial, gw, nw);
     }
+    ws.finish(partial, nsys, gw, nw);
 }
 
 // x += t1 w, w = v + t2 w (FP64) for pairs with a pending update; ||w||^2.
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, double *partial) {
+    WarpSum ws;
     const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -369,7 +658,7 @@ __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const 
                 const int64_t c0 = li * LCOLS, c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 for (int64_t c = c0 + half; c < c1; c += 2) {
                     const int64_t i = c * S.R + j;
-                    const double v = (double)S.V[(int64_t)j * S.n + c] * ia;
+                    const double v = (double)S.V[c * S.RS + j] * ia;
                     double w = S.W[i];
                     if (pend == 2) {
                         w = v;
@@ -383,24 +672,25 @@ __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const 
             }
         }
         ss += __shfl_xor_sync(FULL, ss, 16);
-        if (lane < RMAX) partial[it * RMAX + lane] = ss;
+        ws.add(ss, s, partial, gw, nw);
     }
+    ws.finish(partial, nsys, gw, nw);
 }
 
-// One block of 256 threads per system: thread (l, j) sums the partials of items
-// l, l + 16, ... for right-hand side j, then thread j adds the 16 sums in
+// One block of 256 threads per system: thread (l, j) sums the partials of the
+// producing kernel's warps l, l + 16, ... (G warps) for right-hand side j, then thread j adds the 16 sums in
 // order (deterministic) and advances that pair's scalars; thread 0 finally
 // counts the pairs still iterating.
 constexpr int RED_T = 256;
 
 template <class VT, class ST>
-__global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, const int64_t *beg,
-                                                const double *partial, int phase, int *active_out) {
+__global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, int G, const double *partial,
+                                                int phase, int *active_out) {
     __shared__ double part[RED_T / RMAX][RMAX];
     const int s = blockIdx.x, t = threadIdx.x, j = t % RMAX, l = t / RMAX;
     BSys<VT, ST> &S = sys[s];
     double acc = 0.0;
-    for (int64_t i = beg[s] + l; i < beg[s + 1]; i += RED_T / RMAX) acc += partial[i * RMAX + j];
+    for (int b = l; b < G; b += RED_T / RMAX) acc += partial[((int64_t)s * G + b) * RMAX + j];
     part[l][j] = acc;
     __syncthreads();
     if (t < RMAX && j < S.R) {
@@ -473,6 +763,7 @@ struct BatchWork {
     int *h_active = nullptr;
     LsqrScalars *h_scal = nullptr;
     int64_t nf_items = 0, na_items = 0, nu_items = 0;
+    unsigned gi = 1, gf = 1, ga = 1, gu = 1;   // grids of init / forward / adjoint / update
     std::vector<int64_t> hf, ha, hu;
     std::map<int, cudaGraphExec_t> graphs;
     std::vector<double> tune_ms;
@@ -498,6 +789,11 @@ template <class K> static unsigned bgrid(K kernel, int device, int64_t items) {
     return (unsigned)(g < need ? g : need);
 }
 
+static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// V row stride: R rounded up to 4, 8 or 16 (16-byte groups that divide 16 lanes).
+static int v_stride(int R) { return R <= 4 ? 4 : R <= 8 ? 8 : 16; }
+
 template <class VT, class ST> struct Batched {
     using Sys = BSys<VT, ST>;
 
@@ -509,7 +805,7 @@ template <class VT, class ST> struct Batched {
         for (size_t s = 0; s < hs.size(); ++s) {
             nf[s] = (hs[s]->m + TR - 1) / TR;
             const int64_t nl = ((int64_t)hs[s]->n + LCOLS - 1) / LCOLS;
-            beg[s + 1] = beg[s] + nf[s] + nl;
+            beg[s + 1] = beg[s] + round_up(nf[s] + nl, WPB);
         }
     }
 
@@ -523,13 +819,18 @@ template <class VT, class ST> struct Batched {
         bw->hu.assign(nsys + 1, 0);
         for (int i = 0; i < nsys; ++i) {
             pdst_handle *h = hs[i];
-            bw->ha[i + 1] = bw->ha[i] + h->n_adj;
-            bw->hu[i + 1] = bw->hu[i] + ((int64_t)h->n + LCOLS - 1) / LCOLS;
+            bw->ha[i + 1] = bw->ha[i] + round_up(h->n_adj, WPB);
+            bw->hu[i + 1] = bw->hu[i] + round_up(((int64_t)h->n + LCOLS - 1) / LCOLS, WPB);
         }
         bw->nf_items = bw->hf[nsys];
         bw->na_items = bw->ha[nsys];
         bw->nu_items = bw->hu[nsys];
-        const int64_t maxitems = std::max(bw->nf_items, std::max(bw->na_items, bw->nu_items));
+        const int device = hs[0]->device;
+        bw->gi = bgrid(k_binit<VT, ST>, device, bw->nf_items);
+        bw->gf = bgrid(k_bfwd<VT, ST>, device, bw->nf_items);
+        bw->ga = bgrid(k_badj<VT, ST>, device, bw->na_items);
+        bw->gu = bgrid(k_bupd<VT, ST>, device, bw->nu_items);
+        const int64_t maxg = std::max(std::max(bw->gi, bw->gf), std::max(bw->ga, bw->gu));
         // (re)allocate vectors only on a new batch
         if (bw->bufs.empty()) {
             for (int i = 0; i < nsys; ++i) {
@@ -541,8 +842,12 @@ template <class VT, class ST> struct Batched {
                 PDST_TRY(CP->alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz * RMAX, 1)));
                 PDST_TRY(CD->alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
                 PDST_CUDA(cudaMemsetAsync(CD->p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
-                PDST_TRY(U->alloc(sizeof(ST) * (h->m + h->n) * R));
-                PDST_TRY(V->alloc(sizeof(ST) * (int64_t)h->n * R));
+                const int64_t ubytes = sizeof(ST) * (h->m + h->n) * v_stride(R);
+                PDST_TRY(U->alloc(ubytes));
+                PDST_CUDA(cudaMemsetAsync(U->p, 0, ubytes, s));
+                const int64_t vbytes = sizeof(ST) * std::max<int64_t>((int64_t)h->n * v_stride(R), 1);
+                PDST_TRY(V->alloc(vbytes));
+                PDST_CUDA(cudaMemsetAsync(V->p, 0, vbytes, s));
                 PDST_TRY(X->alloc(sizeof(double) * (int64_t)h->n * R));
                 PDST_TRY(W->alloc(sizeof(double) * (int64_t)h->n * R));
             }
@@ -554,7 +859,7 @@ template <class VT, class ST> struct Batched {
             PDST_CUDA(cudaMallocHost(&bw->h_active, sizeof(int) * nsys));
             PDST_CUDA(cudaMallocHost(&bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX));
         }
-        PDST_TRY(bw->partial.alloc(sizeof(double) * RMAX * std::max<int64_t>(maxitems, 1)));
+        PDST_TRY(bw->partial.alloc(sizeof(double) * RMAX * nsys * maxg * WPB));
         PDST_TRY(bw->fbeg.alloc(sizeof(int64_t) * (nsys + 1)));
         LsqrScalars *scd = bw->scal.as<LsqrScalars>();
         for (int i = 0; i < nsys; ++i) {
@@ -566,6 +871,8 @@ template <class VT, class ST> struct Batched {
             q.ny = h->grid.ny;
             q.nz = h->nz;
             q.R = nrhs[i];
+            q.RS = v_stride(nrhs[i]);
+            q.n_adj = h->n_adj;
             q.row_cptr = h->row_cptr.as<int64_t>();
             q.row_cells = h->row_cells.as<int32_t>();
             q.val = h->vals[dtype].csr.as<VT>();
@@ -618,38 +925,30 @@ template <class VT, class ST> struct Batched {
         return PDST_OK;
     }
 
-    static void launch_iter(BatchWork *bw, int nsys, int device, cudaStream_t s) {
+    static void launch_iter(BatchWork *bw, int nsys, cudaStream_t s) {
         Sys *sys = bw->desc.as<Sys>();
         double *part = bw->partial.as<double>();
-        k_bfwd<VT, ST><<<bgrid(k_bfwd<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
-            sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_FWD,
-                                           bw->active.as<int>());
-        k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
-            sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ,
-                                           bw->active.as<int>());
-        k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
-            sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
-                                           bw->active.as<int>());
+        int *act = bw->active.as<int>();
+        k_bfwd<VT, ST><<<bw->gf, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
+                                             part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gf * WPB), part, PH_FWD, act);
+        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ, act);
+        k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act);
     }
 
-    static pdst_status start(BatchWork *bw, int nsys, int device, cudaStream_t s) {
+    static pdst_status start(BatchWork *bw, int nsys, cudaStream_t s) {
         Sys *sys = bw->desc.as<Sys>();
         double *part = bw->partial.as<double>();
-        k_binit<VT, ST><<<bgrid(k_binit<VT, ST>, device, bw->nf_items), BT, 0, s>>>(
-            sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->fbeg.as<int64_t>(), part, PH_INIT,
-                                           bw->active.as<int>());
-        k_badj<VT, ST><<<bgrid(k_badj<VT, ST>, device, bw->na_items), BT, 0, s>>>(
-            sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->abeg.as<int64_t>(), part, PH_ADJ_INIT,
-                                           bw->active.as<int>());
-        k_bupd<VT, ST><<<bgrid(k_bupd<VT, ST>, device, bw->nu_items), BT, 0, s>>>(
-            sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, bw->ubeg.as<int64_t>(), part, PH_UPD,
-                                           bw->active.as<int>());
+        int *act = bw->active.as<int>();
+        k_binit<VT, ST><<<bw->gi, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
+                                              part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gi * WPB), part, PH_INIT, act);
+        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ_INIT, act);
+        k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act);
         PDST_CUDA(cudaGetLastError());
         return PDST_OK;
     }
@@ -670,13 +969,13 @@ template <class VT, class ST> struct Batched {
         for (int tr : cands) {
             PDST_TRY(prepare(bw, hs, nrhs, dtype, tr, s));
             PDST_TRY(load_inputs(bw, nsys, d_dev, init, s));
-            PDST_TRY(start(bw, nsys, device, s));
+            PDST_TRY(start(bw, nsys, s));
             Sys *sys = bw->desc.as<Sys>();
             float ms = 0.f, tot = 0.f;
             (void)sys;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
-                launch_iter(bw, nsys, device, s);
+                launch_iter(bw, nsys, s);
                 cudaEventRecord(e1, s);
                 PDST_CUDA(cudaEventSynchronize(e1));
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -715,7 +1014,7 @@ template <class VT, class ST> struct Batched {
             }
         }
         PDST_TRY(load_inputs(bw, nsys, d_dev, init, s));
-        PDST_TRY(start(bw, nsys, device, s));
+        PDST_TRY(start(bw, nsys, s));
         launches += 6;
         cudaGraphExec_t exec = nullptr;
         auto it = bw->graphs.find(kblock);
@@ -727,7 +1026,7 @@ template <class VT, class ST> struct Batched {
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                for (int i = 0; i < kblock; ++i) launch_iter(bw, nsys, device, cs);
+                for (int i = 0; i < kblock; ++i) launch_iter(bw, nsys, cs);
                 e = cudaStreamEndCapture(cs, &g);
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
