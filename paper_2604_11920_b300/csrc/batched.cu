@@ -293,7 +293,7 @@ __device__ __forceinline__ void fwd_g_item(const BSys<VT, ST> &S, int64_t li, in
 
 // Forward phase: G rows (fwd_g_item) and the w L rows (column tiles).
 template <class VT, class ST>
-__global__ void __launch_bounds__(BT) k_bfwd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+__global__ void __launch_bounds__(BT, 4) k_bfwd(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int TR, double *partial) {
     using AT = ST;
     WarpSum ws;
