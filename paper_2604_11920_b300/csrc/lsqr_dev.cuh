@@ -85,6 +85,20 @@ __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Bulk prefetch of the bytes [p, p + bytes) into L2 by the copy engine
+// (cp.async.bulk.prefetch.L2: a hint, nothing to wait for).  The range is
+// shrunk to 16-byte boundaries, so it never leaves [p, p + bytes).  One
+// thread issues it; the warp's later loads of the range then hit L2.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint64_t bytes) {
+    const uint64_t a = (uint64_t)__cvta_generic_to_global(p);
+    const uint64_t s = (a + 15u) & ~(uint64_t)15u, e = (a + bytes) & ~(uint64_t)15u;
+    if (e > s) {
+        const uint64_t n = e - s < ((uint64_t)1 << 30) ? e - s : ((uint64_t)1 << 30);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)n)
+                     : "memory");
+    }
+}
+
 // G rows of the forward sweep in the blocked layout.  With nz % 4 == 0 each
 // half-warp owns one row (two rows per warp in flight) and each lane whole
 // runs; the next row's run pointers and first cells are prefetched while the
