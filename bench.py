@@ -41,6 +41,7 @@ FORMS = {
     # name: (dtype, format, precond); precond 1 = column-norm, 2 = learned scaling
     "f64-element": ("f64", "element", 0),
     "f64-blocked": ("f64", "blocked", 0),
+    "df64-blocked": ("df64", "blocked", 0),
     "f32-element": ("f32", "element", 0),
     "f32-blocked": ("f32", "blocked", 0),
     "f32-blocked-colnorm": ("f32", "blocked", 1),
@@ -53,8 +54,8 @@ DEFAULT_FORM = "f32-blocked-learned" if os.path.exists(MODEL_PATH) else "f32-blo
 ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
 TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10)
 REF_TOL = 1e-12                       # FP64 reference solve (stops earlier on S4-S6 if need be)
-VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
-VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4}
+VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "df64": 8}
+VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4, "df64": 8}
 
 
 def parse_args():

@@ -54,7 +54,12 @@ typedef enum {
 typedef enum {
     PDST_F64 = 0,   /* FP64 values, FP64 vectors (the plain form) */
     PDST_F32 = 1,   /* FP32 values, FP32 vectors, FP32 accumulation */
-    PDST_BF16 = 2   /* BF16 values, FP32 vectors, FP32 accumulation */
+    PDST_BF16 = 2,  /* BF16 values, FP32 vectors, FP32 accumulation */
+    PDST_DF64 = 3   /* double-float: each FP64 value kept as a float pair hi + lo
+                       (about 48 significant bits), vectors and accumulation in
+                       the same form, all arithmetic on the FP32 pipe.  Blocked
+                       layout and pdst_lsqr / pdst_lsqr_host only (no counterpart
+                       in the paper: B300's FP64 pipe bounds the PDST_F64 sweeps) */
 } pdst_dtype;
 
 /* Index layout used by the sparse products. */

@@ -32,6 +32,10 @@ static pdst_status values_to_host(int dtype, const void *src, int64_t count, dou
         std::vector<float> tmp(count);
         PDST_CUDA(cudaMemcpy(tmp.data(), src, sizeof(float) * count, cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < count; ++i) out[i] = (double)tmp[i];
+    } else if (dtype == PDST_DF64) {
+        std::vector<dfl> tmp(count);
+        PDST_CUDA(cudaMemcpy(tmp.data(), src, sizeof(dfl) * count, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < count; ++i) out[i] = (double)tmp[i].hi + (double)tmp[i].lo;
     } else {
         std::vector<uint16_t> tmp(count);
         PDST_CUDA(cudaMemcpy(tmp.data(), src, sizeof(uint16_t) * count, cudaMemcpyDeviceToHost));
@@ -76,7 +80,7 @@ extern "C" pdst_status pdst_G_info(pdst_handle_t h, int64_t *m, int32_t *n, int6
 extern "C" pdst_status pdst_G_export_csr(pdst_handle_t h, int32_t dtype, int64_t *row_ptr_host,
                                          int32_t *col_host, double *val_host) {
     PDST_CHECK_ARG(h != nullptr, "pdst_G_export_csr: handle is NULL");
-    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_G_export_csr: unknown dtype");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 3, "pdst_G_export_csr: unknown dtype");
     if (val_host && !h->vals[dtype].present) {
         set_error("pdst_G_export_csr: values of dtype %d were not kept", dtype);
         return PDST_ERR_STATE;
@@ -101,7 +105,7 @@ extern "C" pdst_status pdst_G_export_csr(pdst_handle_t h, int32_t dtype, int64_t
 extern "C" pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t *col_ptr_host,
                                          int32_t *row_host, double *val_host) {
     PDST_CHECK_ARG(h != nullptr, "pdst_G_export_csc: handle is NULL");
-    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_G_export_csc: unknown dtype");
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 3, "pdst_G_export_csc: unknown dtype");
     if (val_host && !h->vals[dtype].present) {
         set_error("pdst_G_export_csc: values of dtype %d were not kept", dtype);
         return PDST_ERR_STATE;
@@ -142,7 +146,7 @@ extern "C" pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t
         }
     }
     if (val_host) {
-        if (elem) {
+        if (elem && dtype != PDST_DF64) {   // no element-CSC copy of the float pairs
             PDST_TRY(values_to_host(dtype, h->vals[dtype].csc.p, h->nnz, val_host));
         } else {
             // reorder the blocked CSC values (cell, row, depth) to column order

@@ -263,6 +263,13 @@ __global__ void k_bcsc_values(int64_t U, int nz, const int64_t *__restrict__ run
     }
 }
 
+// Double-float copy: each FP64 value as its nearest float plus the rest.
+__global__ void k_split_values(int64_t nnz, const double *__restrict__ v, dfl *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dfl(v[i]);
+}
+
 template <class T>
 __global__ void k_csc_values(int64_t U, int nz, const int32_t *__restrict__ cells,
                              const int64_t *__restrict__ run_pos,
@@ -489,22 +496,35 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
 
     // values in CSR order
     const int64_t nnz = h->nnz;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < 4; ++d) {
         if (!(dtypes & (1u << d))) continue;
-        size_t es = d == PDST_F64 ? 8 : d == PDST_F32 ? 4 : 2;
+        size_t es = d == PDST_F64 ? 8 : d == PDST_F32 ? 4 : d == PDST_BF16 ? 2 : sizeof(dfl);
         PDST_TRY(h->vals[d].csr.alloc(es * std::max<int64_t>(nnz, 1)));
         PDST_TRY(h->vals[d].bcsc.alloc(es * std::max<int64_t>(nnz, 1)));
-        if (h->formats & (1u << PDST_FMT_ELEMENT))
+        if ((h->formats & (1u << PDST_FMT_ELEMENT)) && d != PDST_DF64)
             PDST_TRY(h->vals[d].csc.alloc(es * std::max<int64_t>(nnz, 1)));
         h->vals[d].present = true;
+    }
+    // the float pairs are split from the FP64 values (kept or temporary)
+    DevBuf v64_tmp;
+    double *v64 = h->vals[PDST_F64].present ? h->vals[PDST_F64].csr.as<double>() : nullptr;
+    if (h->vals[PDST_DF64].present && !v64 && nnz) {
+        PDST_TRY(v64_tmp.alloc(sizeof(double) * nnz));
+        v64 = v64_tmp.as<double>();
     }
     if (nnz) {
         k_expand_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
             U, nz, d_lens.as<double>(), d_runrow.as<int32_t>(), h->row_period.as<int32_t>(),
-            d_kdz.as<double>(), h->vals[0].present ? h->vals[0].csr.as<double>() : nullptr,
+            d_kdz.as<double>(), v64,
             h->vals[1].present ? h->vals[1].csr.as<float>() : nullptr,
             h->vals[2].present ? h->vals[2].csr.as<__nv_bfloat16>() : nullptr);
         PDST_CUDA(cudaGetLastError());
+        if (h->vals[PDST_DF64].present) {
+            k_split_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
+                nnz, v64, h->vals[PDST_DF64].csr.as<dfl>());
+            PDST_CUDA(cudaGetLastError());
+        }
+        PDST_CUDA(cudaStreamSynchronize(s));   // the temporary is released on scope exit
     }
 
     // cell-level transpose
@@ -561,6 +581,9 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
                                                      h->vals[1].csr.as<float>(),
                                                      h->vals[1].csc.as<float>());
         }
+        if (h->vals[PDST_DF64].present)
+            k_bcsc_values<dfl><<<g, 256, 0, s>>>(U, nz, rp, h->vals[PDST_DF64].csr.as<dfl>(),
+                                                h->vals[PDST_DF64].bcsc.as<dfl>());
         if (h->vals[2].present) {
             k_bcsc_values<__nv_bfloat16><<<g, 256, 0, s>>>(U, nz, rp,
                                                           h->vals[2].csr.as<__nv_bfloat16>(),
@@ -662,7 +685,7 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
                                                  : (1u << PDST_F64) | (1u << PDST_F32);
     uint32_t formats = opts && opts->formats ? opts->formats
                                              : (1u << PDST_FMT_ELEMENT) | (1u << PDST_FMT_BLOCKED);
-    PDST_CHECK_ARG((dtypes & ~7u) == 0, "pdst_build_G: unknown value dtype bits");
+    PDST_CHECK_ARG((dtypes & ~15u) == 0, "pdst_build_G: unknown value dtype bits");
     PDST_CHECK_ARG((formats & ~3u) == 0, "pdst_build_G: unknown format bits");
 
     static std::atomic<uint64_t> next_uid{1};

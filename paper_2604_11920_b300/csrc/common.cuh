@@ -99,6 +99,19 @@ struct LsqrSync {
     unsigned int count[8];
 };
 
+// Double-float number hi + lo (two floats; arithmetic in dfloat.cuh).  Trivial
+// default constructor, so it can live in shared memory and in device arrays.
+struct __align__(8) dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ constexpr dfl(float v) : hi(v), lo(0.f) {}
+    // nearest float, then the rest (v - hi is exact in FP64)
+    __host__ __device__ dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
 struct ValueSet {
     DevBuf csr;   // values in CSR order (row-major, cells ascending, depth fastest)
     DevBuf csc;   // element CSC order: column j = h*nz+k at nz*cell_rptr[h] + k*cnt[h]
@@ -150,7 +163,7 @@ struct pdst_handle {
     pdst::DevBuf col;          // int32 [nnz]
     pdst::DevBuf col_ptr;      // int64 [n+1]
     pdst::DevBuf row_idx;      // int32 [nnz]
-    pdst::ValueSet vals[3];    // by pdst_dtype
+    pdst::ValueSet vals[4];    // by pdst_dtype
 
     pdst::DevBuf colscale;     // double [n] right diagonal scaling D
     bool has_colscale = false;

@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_fwd(OpArgs<VT, 
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
-    if (FMT == FMT_BLK) {
+    if constexpr (FMT == FMT_BLK) {
         ss = fwd_rows_blk<VT, ST>(a, ia, cu, gw, nw, lane);
     } else {
         for (int64_t r = gw; r < a.m; r += nw) {
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
     if (!skip) {
-        if (FMT == FMT_BLK) {
+        if constexpr (FMT == FMT_BLK) {
             ss = (a.nz & 3) == 0 && a.nz <= 64
                      ? adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane)
                      : adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
@@ -1026,7 +1026,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     pdst_lsqr_opts_default(&opts);
     if (o) opts = *o;
     const int dtype = opts.dtype, fmt = opts.format;
-    PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_lsqr: unknown dtype %d", dtype);
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 3, "pdst_lsqr: unknown dtype %d", dtype);
     PDST_CHECK_ARG(fmt == PDST_FMT_ELEMENT || fmt == PDST_FMT_BLOCKED, "pdst_lsqr: unknown format");
     PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr: itmax must be >= 0");
     PDST_CHECK_ARG(std::isfinite(w_s) && w_s >= 0.0, "pdst_lsqr: w must be finite and >= 0");
@@ -1055,8 +1055,13 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
                    opts.precond);
     PDST_CHECK_ARG(opts.refine >= 0 && opts.refine <= 100, "pdst_lsqr: refine must be in 0..100");
     const bool refine = opts.refine > 0;
-    PDST_CHECK_ARG(opts.refine_dtype >= -1 && opts.refine_dtype <= 2,
+    PDST_CHECK_ARG(opts.refine_dtype >= -1 && opts.refine_dtype <= 3,
                    "pdst_lsqr: unknown refine_dtype %d", opts.refine_dtype);
+    if ((dtype == PDST_DF64 || (refine && opts.refine_dtype == PDST_DF64)) &&
+        fmt != PDST_FMT_BLOCKED) {
+        set_error("pdst_lsqr: the double-float form runs on the blocked layout only");
+        return PDST_ERR_ARG;
+    }
     if (refine && opts.refine_dtype >= 0 && !h->vals[opts.refine_dtype].present) {
         set_error("pdst_lsqr: values of refine_dtype %d were not kept", opts.refine_dtype);
         return PDST_ERR_STATE;
@@ -1110,6 +1115,10 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
 
     auto solve_once = [&](const double *baug, bool accumulate, bool fresh_,
                           int dtype) -> pdst_status {
+        if (dtype == PDST_DF64)
+            return dispatch_run<dfl, dfl, FMT_BLK>(h, w, dtype, scaled, lamrows, d_dev, init,
+                                                   kblock, ug, prof, m_out, s, fresh_, rs, baug,
+                                                   accumulate, Dover);
         if (dtype == PDST_F64)
             return fmt == PDST_FMT_ELEMENT
                        ? dispatch_run<double, double, FMT_ELEM>(h, w, dtype, scaled, lamrows, d_dev,

@@ -6,6 +6,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace pdst {
 
@@ -15,6 +16,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // lane to cover HBM latency at 32 resident warps per SM.
 template <class AT> struct Unroll { static constexpr int U = 4; };
 template <> struct Unroll<double> { static constexpr int U = 2; };
+template <> struct Unroll<dfl> { static constexpr int U = 2; };
 
 
 // ------------------------------------------------------------ load helpers
@@ -42,6 +44,14 @@ template <> struct Pack4<__nv_bfloat16> {
         v[3] = __uint_as_float(t.y & 0xffff0000u);
     }
 };
+template <> struct Pack4<dfl> {
+    static __device__ __forceinline__ void ld(const dfl *p, dfl v[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = dfl(a.x, a.y); v[1] = dfl(a.z, a.w); v[2] = dfl(b.x, b.y); v[3] = dfl(b.z, b.w);
+    }
+};
+
 template <class VT> struct Wide { using T = VT; };
 template <> struct Wide<__nv_bfloat16> { using T = float; };
 
@@ -56,7 +66,14 @@ template <> __device__ __forceinline__ void ldx4<double>(const double *p, double
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+template <> __device__ __forceinline__ void ldx4<dfl>(const dfl *p, dfl v[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = dfl(a.x, a.y); v[1] = dfl(a.z, a.w); v[2] = dfl(b.x, b.y); v[3] = dfl(b.z, b.w);
+}
+
 __device__ __forceinline__ float ldval(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ dfl ldval(const dfl *p) { return __ldcs(p); }
 __device__ __forceinline__ double ldval(const double *p) { return __ldcs(p); }
 __device__ __forceinline__ float ldval(const __nv_bfloat16 *p) {
     return __bfloat162float(*p);

@@ -18,9 +18,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpdst.so")
 
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, DF64 = 0, 1, 2, 3
 FMT_ELEMENT, FMT_BLOCKED = 0, 1
-DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
 FORMATS = {"element": FMT_ELEMENT, "blocked": FMT_BLOCKED}
 
 STATUS = {0: "PDST_OK", 1: "PDST_ERR_ARG", 2: "PDST_ERR_CUDA", 3: "PDST_ERR_OOM",

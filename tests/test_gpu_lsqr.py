@@ -29,7 +29,7 @@ def tiny():
     G = oracle.build_G_problem(p)
     GT = oracle.transpose(G)
     d = oracle.rhs_for(p, G)
-    h = pdst.build_G_problem(p, dtypes=("f64", "f32", "bf16"))
+    h = pdst.build_G_problem(p, dtypes=("f64", "f32", "bf16", "df64"))
     ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=1e-12, btol=1e-12,
                       itmax=50000)
     return p, G, GT, d, h, ref
@@ -224,3 +224,94 @@ def test_two_phase_solve_reaches_fp64_solution(tiny, dtype, precond):
     again = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype=dtype, fmt="blocked",
                    precond=precond, refine=3, refine_dtype="f64", refine_tol=1e-10)
     assert np.array_equal(again.m.cpu().numpy(), res.m.cpu().numpy())
+
+
+# ------------------------------------------------------------ double-float form
+# Each FP64 value is held as hi + lo (two floats) and the sweeps run in
+# double-float arithmetic: relative rounding about 2^-47 per operation instead
+# of FP64's 2^-53.  Bars: 1e-9 on fixed-k iterates (sums of ~10^3 products per
+# row, k <= 8 steps of a well-conditioned bidiagonalisation), the parity bar on
+# converged solutions.
+
+DF_ITER_TOL = 1e-9
+
+
+def test_df64_values_split_exactly(tiny):
+    """hi = fl32(v), lo = fl32(v - hi): |v - (hi + lo)| <= 2^-48 |v| for every stored value."""
+    p, G, GT, d, h, _ = tiny
+    ptr, idx, v64 = h.export_csr("f64")
+    _, _, vdf = h.export_csr("df64")
+    assert np.array_equal(v64, G.val)
+    err = np.abs(vdf - v64)
+    assert np.all(err <= 2.0 ** -48 * np.abs(v64))
+    assert np.any(err > 0)       # the pairs do carry the bits below float precision
+    nzm = v64 != 0
+    assert np.max(np.abs(vdf - v64.astype(np.float32))[nzm] / np.abs(v64[nzm])) > 1e-9
+    _, _, cdf = h.export_csc("df64")
+    _, _, c64 = h.export_csc("f64")
+    assert np.all(np.abs(cdf - c64) <= 2.0 ** -48 * np.abs(c64))
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_fixed_k_iterates_df64(tiny, k):
+    p, G, GT, d, h, _ = tiny
+    ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=0, btol=0, conlim=0,
+                      itmax=k)
+    res = h.lsqr(to_dev(d), p.w, p.lam, k, 0.0, dtype="df64", fmt="blocked", conlim=1e300)
+    assert res.info["iters"] == k and res.info["istop"] == 7
+    assert rel(res.m.cpu().numpy(), ref.x) < DF_ITER_TOL
+    for key in ("rnorm", "arnorm", "anorm", "acond", "xnorm", "bnorm"):
+        assert abs(res.info[key] - getattr(ref, key)) <= DF_ITER_TOL * abs(getattr(ref, key)), key
+    # FP32 values are far from this bar at the same k
+    f32 = h.lsqr(to_dev(d), p.w, p.lam, k, 0.0, dtype="f32", fmt="blocked", conlim=1e300)
+    if k >= 2:
+        assert rel(f32.m.cpu().numpy(), ref.x) > 100 * rel(res.m.cpu().numpy(), ref.x)
+
+
+def test_converged_df64_matches_oracle(tiny):
+    p, G, GT, d, h, ref = tiny
+    res = h.lsqr(to_dev(d), p.w, p.lam, 50000, 1e-12, dtype="df64", fmt="blocked")
+    assert res.info["istop"] in (1, 2)
+    e = rel(res.m.cpu().numpy(), ref.x)
+    assert e <= MODEL_TOL
+    r_gpu = residual_norm(p, G, res.m.cpu().numpy(), d, p.lam)
+    r_ref = residual_norm(p, G, ref.x, d, p.lam)
+    assert abs(r_gpu - r_ref) / r_ref <= RESID_TOL
+    # same solve in FP64 on the GPU: the two agree far inside the parity bar
+    f64 = h.lsqr(to_dev(d), p.w, p.lam, 50000, 1e-12, dtype="f64", fmt="blocked")
+    assert rel(res.m.cpu().numpy(), f64.m.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype,precond", [("f32", 0), ("f32", 1)])
+def test_two_phase_with_df64_refinement(tiny, dtype, precond):
+    """FP32 solve, then double-float refinement sweeps on the FP64 residual:
+    the same accuracy as FP64 refinement sweeps."""
+    p, G, GT, d, h, ref = tiny
+    if precond:
+        h.set_col_scaling(None, p.w, p.lam)
+    r64 = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype=dtype, fmt="blocked", precond=precond,
+                 refine=3, refine_dtype="f64", refine_tol=1e-10)
+    rdf = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype=dtype, fmt="blocked", precond=precond,
+                 refine=3, refine_dtype="df64", refine_tol=1e-10)
+    e64 = rel(r64.m.cpu().numpy(), ref.x)
+    edf = rel(rdf.m.cpu().numpy(), ref.x)
+    print(f"{dtype} precond={precond}: FP64 sweeps {e64:.2e}, double-float sweeps {edf:.2e} "
+          f"({rdf.info['sweeps']} sweeps, {rdf.info['iters']} it)")
+    assert rdf.info["sweeps"] >= 2
+    assert edf <= 1e-6
+    assert edf <= 10 * e64 + 1e-9
+
+
+def test_df64_form_errors(tiny):
+    p, G, GT, d, h, _ = tiny
+    with pytest.raises(pdst.PdstError):
+        h.lsqr(to_dev(d), p.w, p.lam, 10, 1e-6, dtype="df64", fmt="element")
+    with pytest.raises(pdst.PdstError):
+        h.lsqr(to_dev(d), p.w, p.lam, 10, 1e-6, dtype="f32", fmt="element", refine=2,
+               refine_dtype="df64")
+    with pytest.raises(pdst.PdstError):
+        h.apply_G(to_dev(np.zeros(p.n)), to_dev(np.zeros(h.m)), dtype="df64")
+    h2 = pdst.build_G_problem(p, dtypes=("f32",))
+    with pytest.raises(pdst.PdstError):
+        h2.lsqr(to_dev(d), p.w, p.lam, 10, 1e-6, dtype="df64", fmt="blocked")
+    h2.close()
