@@ -76,6 +76,10 @@ def parse_args():
     ap.add_argument("--batched-systems", type=int, default=64)
     ap.add_argument("--only-batched", action="store_true",
                     help="print the batched-workload section alone")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy-matched ladder (large systems)")
+    ap.add_argument("--ref-tol", type=float, default=REF_TOL,
+                    help="tolerance of the FP64 reference solve")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the chosen form only (for profiler runs)")
     ap.add_argument("--ncu-case", action="store_true",
@@ -314,7 +318,7 @@ def run_pdst(args, rank, world):
         ms_plain, res_plain = ms, res
     m_plain = res_plain.m.clone()
     # FP64 reference solution: plain form at tol REF_TOL (its iteration count is reported)
-    ref = h.lsqr(d, p.w, p.lam, 200000, REF_TOL, dtype="f64", fmt="element")
+    ref = h.lsqr(d, p.w, p.lam, 200000, args.ref_tol, dtype="f64", fmt="element")
 
     def relerr(a):
         return float(torch.linalg.norm(a - ref.m) / torch.linalg.norm(ref.m))
@@ -353,12 +357,15 @@ def run_pdst(args, rank, world):
                         "sweeps": r.info["sweeps"], "model_error": err}
         return {"s": None, "iters": None, "model_error": err}
 
-    acc_chosen = to_accuracy(args.form)
-    acc_plain = to_accuracy(PLAIN)
-    accuracy_matched = {"target_model_error": ACC_TARGET, "chosen": acc_chosen,
-                        "plain_fp64": acc_plain,
-                        "speedup": (acc_plain["s"] / acc_chosen["s"])
-                        if acc_plain["s"] and acc_chosen["s"] else None}
+    if args.no_accuracy:
+        accuracy_matched = None
+    else:
+        acc_chosen = to_accuracy(args.form)
+        acc_plain = to_accuracy(PLAIN)
+        accuracy_matched = {"target_model_error": ACC_TARGET, "chosen": acc_chosen,
+                            "plain_fp64": acc_plain,
+                            "speedup": (acc_plain["s"] / acc_chosen["s"])
+                            if acc_plain["s"] and acc_chosen["s"] else None}
 
     # per-kernel device time (events around each launch, same solve)
     prof = solve(args.form, profile=True)
@@ -408,7 +415,7 @@ def run_pdst(args, rank, world):
                "d2h_bytes_per_step": 8 * h.n}
 
     out.update({
-        "reference": {"form": PLAIN, "tol": REF_TOL, "iters": ref.info["iters"],
+        "reference": {"form": PLAIN, "tol": args.ref_tol, "iters": ref.info["iters"],
                       "istop": ref.info["istop"]},
         "config": {"workload": workload_desc(p), "form": args.form,
                    "plain_form": PLAIN, "nnz": h.nnz,

@@ -48,6 +48,7 @@ template <class VT, class ST> struct BSys {
     const int32_t *cell_order;
     const VT *valB;   // blocked CSC values
     const int32_t *adj_item;   // (cell, first row) per adjoint work item
+    int32_t adj_chunk;         // rows per adjoint work item
     ST *chunk_part;   // adjoint work items x nz x RMAX partial sums
     unsigned *cell_done;       // H finished-chunk counters
     ST *U;            // (m + n) x RS, right-hand side fastest (padding lanes stay 0)
@@ -407,7 +408,7 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
     const int q0 = __ldg(S.adj_item + 2 * li + 1);
     const int64_t c0 = __ldg(S.cell_rptr + h);
     const int cnt = __ldg(S.cell_cnt + h);
-    const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
+    const int q1 = q0 + S.adj_chunk < cnt ? q0 + S.adj_chunk : cnt;
     const int32_t *rows = S.cell_rows + c0;
     const VT *vb = S.valB + c0 * NZC + 4 * kq;
     const ST *ub = S.U + 4 * g;
@@ -448,7 +449,7 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] += __shfl_xor_sync(FULL, acc[a][b], off);
-    const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+    const int nch = cnt > S.adj_chunk ? (cnt + S.adj_chunk - 1) / S.adj_chunk : 1;
     bool finish = true;
     if (nch > 1) {
         ST *cp = S.chunk_part;
@@ -460,7 +461,7 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
                     cp[(li * NZC + 4 * kq + a) * RMAX + 4 * g + b] = acc[a][b];
         finish = adj_last_chunk(S.cell_done, h, nch, lane, flag);
         if (finish) {
-            const int64_t first = li - q0 / ADJ_CHUNK;
+            const int64_t first = li - q0 / S.adj_chunk;
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -535,7 +536,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
     const int q0 = __ldg(S.adj_item + 2 * li + 1);
     const int64_t c0 = __ldg(S.cell_rptr + h);
     const int cnt = __ldg(S.cell_cnt + h);
-    const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
+    const int q1 = q0 + S.adj_chunk < cnt ? q0 + S.adj_chunk : cnt;
     const int32_t *rows = S.cell_rows + c0;
     const VT *vb = S.valB + c0 * nz;
     AT acc[BNZ];
@@ -567,7 +568,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
     }
 #pragma unroll
     for (int k = 0; k < BNZ; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], 16);
-    const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+    const int nch = cnt > S.adj_chunk ? (cnt + S.adj_chunk - 1) / S.adj_chunk : 1;
     bool finish = true;
     if (nch > 1) {
         ST *cp = S.chunk_part;
@@ -577,7 +578,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
                 if (k < nz) cp[(li * nz + k) * RMAX + j] = acc[k];
         finish = adj_last_chunk(S.cell_done, h, nch, lane, flag);
         if (finish) {
-            const int64_t first = li - q0 / ADJ_CHUNK;
+            const int64_t first = li - q0 / S.adj_chunk;
 #pragma unroll
             for (int k = 0; k < BNZ; ++k) {
                 if (k >= nz) continue;
@@ -606,7 +607,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
     return ss;
 }
 
-// Adjoint phase: work item = a chunk of up to ADJ_CHUNK rows of one cell of
+// Adjoint phase: work item = a chunk of up to adj_chunk rows of one cell of
 // one system (the handle's adjoint work list).  A cell split over several
 // chunks is finished by its last chunk (chunk order sums).
 template <class VT, class ST>
@@ -888,6 +889,7 @@ template <class VT, class ST> struct Batched {
             q.chunk_part = bw->bufs[NB * i + 4]->as<ST>();
             q.cell_done = bw->bufs[NB * i + 5]->as<unsigned>();
             q.adj_item = h->adj_item.as<int32_t>();
+            q.adj_chunk = h->adj_chunk;
             q.sc = scd + (size_t)i * RMAX;
             q.nf = nf[i];
             q.active = 0;

@@ -263,6 +263,29 @@ __global__ void k_bcsc_values(int64_t U, int nz, const int64_t *__restrict__ run
     }
 }
 
+// Rows per adjoint work item.  A cell split over several items pays for its
+// partial sums, a fence and a counter per item, which costs about as much as
+// streaming a few hundred rows, so items are made as long as the load balance
+// allows: the largest power of two in [ADJ_CHUNK_MIN, ADJ_CHUNK_MAX] that still
+// gives at least ITEMS_PER_WARP items to each resident warp of the adjoint
+// sweep (32 per SM).  Measured on B300 (FP32 sweep): 512 rows best on the
+// 64 x 64 x 16 system, 2048 on the 100 x 100 x 20 one; both are this rule's
+// choice.
+constexpr int ITEMS_PER_WARP = 2;
+
+static int choose_adj_chunk(const std::vector<int32_t> &cnt, int sms) {
+    const int64_t target = (int64_t)sms * 32 * ITEMS_PER_WARP;
+    int chunk = ADJ_CHUNK_MIN;
+    while (chunk < ADJ_CHUNK_MAX) {
+        const int64_t next = 2 * (int64_t)chunk;
+        int64_t items = 0;
+        for (int32_t c : cnt) items += std::max<int64_t>(1, (c + next - 1) / next);
+        if (items < target) break;
+        chunk *= 2;
+    }
+    return chunk;
+}
+
 // Double-float copy: each FP64 value as its nearest float plus the rest.
 __global__ void k_split_values(int64_t nnz, const double *__restrict__ v, dfl *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
@@ -633,11 +656,12 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
         PDST_CUDA(cudaMemcpy(h->cell_order.p, order.data(), sizeof(int32_t) * H,
                              cudaMemcpyHostToDevice));
         // adjoint work items: every cell (empty ones too) in chunks of
-        // ADJ_CHUNK rows, cells longest first, chunks of a cell consecutive
+        // adj_chunk rows, cells longest first, chunks of a cell consecutive
+        h->adj_chunk = choose_adj_chunk(cnt, num_sms(h->device));
         std::vector<int32_t> items;
         for (int i = 0; i < H; ++i) {
             const int c = order[i];
-            for (int q0 = 0; q0 < std::max(cnt[c], 1); q0 += ADJ_CHUNK) {
+            for (int q0 = 0; q0 < std::max(cnt[c], 1); q0 += h->adj_chunk) {
                 items.push_back(c);
                 items.push_back(q0);
             }

@@ -121,7 +121,10 @@ struct ValueSet {
     bool present = false;
 };
 
-constexpr int ADJ_CHUNK = 256;   // rows of one cell per adjoint work item
+// Rows of one cell per adjoint work item: chosen per handle at assembly
+// (adj_chunk_rows) between these bounds.
+constexpr int ADJ_CHUNK_MIN = 256;
+constexpr int ADJ_CHUNK_MAX = 2048;
 
 struct LsqrWork;   // lsqr.cu
 
@@ -157,6 +160,7 @@ struct pdst_handle {
     pdst::DevBuf cell_cnt;     // int32 [H]    rows per cell
     pdst::DevBuf cell_order;   // int32 [H]    cells by descending row count (work order)
     pdst::DevBuf adj_item;     // int32 [2*n_adj]  (cell, first row) of each adjoint work item
+    int32_t adj_chunk = 256;   // rows of one cell per adjoint work item
     int64_t n_adj = 0;         // adjoint work items: chunks of ADJ_CHUNK rows, longest cells first
     // element indices (PDST_FMT_ELEMENT)
     pdst::DevBuf row_ptr;      // int64 [m+1]

@@ -50,6 +50,7 @@ template <class VT, class ST> struct OpArgs {
     const VT *valT;           // element CSC order (element layout only)
     const VT *valB;           // blocked CSC order
     const int32_t *adj_item;  // (cell, first row) per adjoint work item
+    int32_t adj_chunk;        // rows per adjoint work item
     int64_t n_adj;
     ST *chunk_part;           // n_adj x nz partial column sums (multi-chunk cells)
     unsigned *cell_done;      // H finished-chunk counters
@@ -332,7 +333,7 @@ __device__ __forceinline__ double adj_finish(const OpArgs<VT, ST> &a, int64_t j,
 }
 
 // G^T rows of the adjoint sweep in the blocked CSC layout.  Work item = a
-// chunk of up to ADJ_CHUNK rows of one cell (cells longest first).  A row's
+// chunk of up to adj_chunk rows of one cell (cells longest first).  A row's
 // nz values are contiguous, so L = nz / G lanes share a row, each reading G
 // consecutive depths (G = 4: one 16-byte vector) and the row's u once
 // (broadcast); 32 / L rows per step, UN steps of loads in flight, row
@@ -360,7 +361,7 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
         const int q0 = __ldg(a.adj_item + 2 * it + 1);
         const int64_t c0 = __ldg(a.cell_rptr + h);
         const int cnt = __ldg(a.cell_cnt + h);
-        const int q1 = q0 + ADJ_CHUNK < cnt ? q0 + ADJ_CHUNK : cnt;
+        const int q1 = q0 + a.adj_chunk < cnt ? q0 + a.adj_chunk : cnt;
         const int32_t *rows = a.cell_rows + c0;
         const VT *vb = a.valB + c0 * nz + G * gi;
         AT acc[G];
@@ -429,10 +430,10 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
             }
         }
         __syncwarp();
-        const int nch = cnt > ADJ_CHUNK ? (cnt + ADJ_CHUNK - 1) / ADJ_CHUNK : 1;
+        const int nch = cnt > a.adj_chunk ? (cnt + a.adj_chunk - 1) / a.adj_chunk : 1;
         bool finish = true;
         if (nch > 1) {
-            const int64_t first = it - q0 / ADJ_CHUNK;
+            const int64_t first = it - q0 / a.adj_chunk;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int k = lane + 32 * half;
@@ -780,6 +781,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     a.valT = h->vals[dtype].csc.as<VT>();
     a.valB = h->vals[dtype].bcsc.as<VT>();
     a.adj_item = h->adj_item.as<int32_t>();
+    a.adj_chunk = h->adj_chunk;
     a.n_adj = h->n_adj;
     a.D = scaled ? h->colscale.as<double>() : nullptr;
     a.lam_rows_on = lamrows ? 1 : 0;

@@ -208,12 +208,14 @@ class Handle:
         return self._ptr
 
     # -- inspection -------------------------------------------------------
-    def export_csr(self, dtype="f64"):
+    def export_csr(self, dtype="f64", ptr_only=False):
+        """(row_ptr, col, val) on the host; ptr_only: row_ptr alone (idx, val = None)."""
         ptr = np.zeros(self.m + 1, np.int64)
-        idx = np.zeros(self.nnz, np.int32)
-        val = np.zeros(self.nnz, np.float64)
-        _check(load().pdst_G_export_csr(self.ptr, DTYPES[dtype], _np_ptr(ptr), _np_ptr(idx),
-                                        _np_ptr(val)))
+        idx = None if ptr_only else np.zeros(self.nnz, np.int32)
+        val = None if ptr_only else np.zeros(self.nnz, np.float64)
+        _check(load().pdst_G_export_csr(self.ptr, DTYPES[dtype], _np_ptr(ptr),
+                                        None if idx is None else _np_ptr(idx),
+                                        None if val is None else _np_ptr(val)))
         return ptr, idx, val
 
     def export_csc(self, dtype="f64"):
