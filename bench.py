@@ -88,6 +88,16 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest value over the ranks: the slowest replica sets the job time."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_problem(name, rank):
     from paper_2604_11920_b300 import synth
     return {"mid": synth.mid, "tiny": synth.tiny, "large": synth.large}[name](
@@ -288,11 +298,7 @@ def run_pdst(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
         return ms, r, launches
 
     with ClockSampler(dev, enabled=not args.no_clocks) as clk:
@@ -406,11 +412,7 @@ def run_pdst(args, rank, world):
             h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_,
                         precond=min(pc_, 1))
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * h.m,
                "d2h_bytes_per_step": 8 * h.n}
 
