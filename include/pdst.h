@@ -156,7 +156,18 @@ typedef struct {
                           early when a sweep needs no iteration.  0 (default): one solve. */
     int32_t refine_dtype; /* pdst_dtype of sweeps 1.. (-1, default: dtype) */
     double refine_tol; /* tolerance of sweeps 1.. (default 1e-5) */
+    int32_t method;    /* PDST_LSQR (default) or PDST_LSMR: the same Golub-Kahan sweeps,
+                          the recurrence and x update of LSQR (Paige & Saunders 1982) or
+                          of LSMR (Fong & Saunders 2011, the solver pDSurfTomo uses).  LSMR
+                          reports ||r|| and ||A^T r|| from its own recurrences, ||x|| from
+                          x, cond(A) as max/min of its second rotation's diagonal; same
+                          stopping tests and istop numbering.  Not available in
+                          pdst_lsqr_noalloc. */
+    int32_t reserved0;
 } pdst_lsqr_opts;
+
+/* Krylov method of pdst_lsqr (pdst_lsqr_opts.method). */
+typedef enum { PDST_LSQR = 0, PDST_LSMR = 1 } pdst_method;
 
 /* Fill *o with the defaults listed above. */
 void pdst_lsqr_opts_default(pdst_lsqr_opts *o);

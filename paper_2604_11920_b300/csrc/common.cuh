@@ -91,7 +91,14 @@ struct LsqrScalars {
     double w_smooth;               // smoothing weight w
     double lam_rows;               // lambda of the appended lambda*D rows (scaled form)
     double *hist;                  // optional ||r|| history (device)
+    // LSMR (Fong & Saunders 2011): rotation state, ||r|| estimate state,
+    // ||A|| and cond(A) accumulators, third update coefficient
+    double alphabar, zetabar, cbar, sbar, rho_prev, rhobar_prev;
+    double betadd, betad, rhod_prev, tautilde_prev, thetatilde, zeta_prev, dsum;
+    double anorm2, rbar_max, rbar_min;
+    double t3;                     // LSMR: h = v - t3 h (t1: h-bar, t2: x)
     int32_t itn, itmax, istop, pending, done, err;
+    int32_t method;                // 0 LSQR, 1 LSMR
 };
 
 // "Last block" counters of the reduction kernels.

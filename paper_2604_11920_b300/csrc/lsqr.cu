@@ -49,6 +49,7 @@ template <class VT, class ST> struct OpArgs {
     const VT *val;            // CSR order
     const VT *valT;           // element CSC order (element layout only)
     const VT *valB;           // blocked CSC order
+    double *hbar;             // LSMR h-bar (n)
     const int32_t *adj_item;  // (cell, first row) per adjoint work item
     int32_t adj_chunk;        // rows per adjoint work item
     int64_t n_adj;
@@ -637,24 +638,56 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
             sc->rhobar = an;
             sc->arnorm = an * beta;
             sc->pending = 2;
+            if (sc->method == 1) lsmr_init(sc, an);
             if (!(sc->arnorm > 0.0)) sc->done = 1;
+        } else if (sc->method == 1) {
+            lsmr_step(sc, an);
         } else {
             lsqr_step(sc, an);
         }
     }
 }
 
-// x += t1 w; w = v + t2 w (FP64), v = v-bar/alpha;  ||w||^2.
+// LSQR: x += t1 w; w = v + t2 w (FP64), v = v-bar/alpha;  ||w||^2.
+// LSMR (wv holds h): hbar = h - t1 hbar; x += t2 hbar; h = v - t3 h;  ||x||^2,
+// then the stopping tests on the new ||x|| (last block).
 template <class ST>
 __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vbar, double *x,
-                                            double *wv, double *partial, LsqrScalars *sc,
-                                            LsqrSync *sy) {
+                                            double *wv, double *hbar, double *partial,
+                                            LsqrScalars *sc, LsqrSync *sy) {
     const int pend = sc->pending;
     if (!pend) return;
     const double alpha = sc->alpha;
     const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
     const double t1 = sc->t1, t2 = sc->t2;
     double ss = 0.0;
+    if (sc->method == 1) {
+        const double t3 = sc->t3;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const double v = (double)vbar[j] * ia;
+            double h = wv[j], xj = x[j];
+            if (pend == 2) {
+                h = v;
+                hbar[j] = 0.0;
+            } else {
+                const double hb = h - t1 * hbar[j];
+                hbar[j] = hb;
+                xj += t2 * hb;
+                x[j] = xj;
+                h = v - t3 * h;
+            }
+            wv[j] = h;
+            ss += xj * xj;
+        }
+        double tot;
+        if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot) && threadIdx.x == 0) {
+            sc->xnorm = sqrt(tot);
+            if (pend != 2) stop_tests(sc);
+            sc->pending = 0;
+        }
+        return;
+    }
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double v = (double)vbar[j] * ia;
@@ -745,7 +778,7 @@ struct LsqrWork {
     int dtype = -1, format = -1, lamrows = -1;
     const void *graph_D = nullptr;
     int64_t M = 0;
-    DevBuf ubar, vbar, vsc, x, wv, partial, scal, sync, chunk_part, cell_done;
+    DevBuf ubar, vbar, vsc, x, wv, hbar, partial, scal, sync, chunk_part, cell_done;
     DevBuf ones, baug, corr;         // refinement: unit scaling, augmented residual, norms
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
@@ -791,6 +824,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
         a.vsc = scaled ? w->vsc.as<ST>() : w->vbar.as<ST>();
         a.x = w->x.as<double>();
         a.wv = w->wv.as<double>();
+        a.hbar = w->hbar.as<double>();
         a.partial = w->partial.as<double>();
         a.sc = w->scal.as<LsqrScalars>();
         a.sy = w->sync.as<LsqrSync>();
@@ -825,6 +859,7 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_TRY(w->vsc.alloc(sizeof(ST) * std::max<int32_t>(h->n, 1)));
         PDST_TRY(w->x.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
         PDST_TRY(w->wv.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
+        PDST_TRY(w->hbar.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
         PDST_TRY(w->partial.alloc(sizeof(double) * 3 * MAXBLK));
         PDST_TRY(w->scal.alloc(sizeof(LsqrScalars)));
         PDST_TRY(w->sync.alloc(sizeof(LsqrSync)));
@@ -842,7 +877,7 @@ template <class VT, class ST, int FMT> struct Solver {
     static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
         k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
         k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
-        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
     }
 
     // Per-kernel device time of `iters` plain-launched iterations, each kernel
@@ -857,7 +892,7 @@ template <class VT, class ST, int FMT> struct Solver {
             cudaEventRecord(ev[4 * i + 1], s);
             k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
             cudaEventRecord(ev[4 * i + 2], s);
-            k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+            k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
             cudaEventRecord(ev[4 * i + 3], s);
         }
         PDST_CUDA(cudaGetLastError());
@@ -892,7 +927,7 @@ template <class VT, class ST, int FMT> struct Solver {
         k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, baug, a.ubar, a.x, a.wv, a.partial, a.sc,
                                         a.sy);
         k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
-        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.partial, a.sc, a.sy);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
         PDST_CUDA(cudaGetLastError());
         rs.launches += 3;
 
@@ -1073,6 +1108,8 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         return PDST_ERR_STATE;
     }
     PDST_CHECK_ARG(!(refine && opts.profile), "pdst_lsqr: profile and refine are exclusive");
+    PDST_CHECK_ARG(opts.method == PDST_LSQR || opts.method == PDST_LSMR,
+                   "pdst_lsqr: unknown method %d", opts.method);
     // refinement sweeps solve for a correction with a full augmented right-hand
     // side, so they always use the form with explicit lambda rows (unit scaling
     // when none is set)
@@ -1092,6 +1129,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     init.w_smooth = w_s;
     init.itmax = itmax;
     init.hist = opts.rnorm_hist_dev;
+    init.method = opts.method;
 
     if (!h->work) h->work = new LsqrWork();
     LsqrWork *w = h->work;
@@ -1319,6 +1357,8 @@ extern "C" void pdst_lsqr_opts_default(pdst_lsqr_opts *o) {
     o->rnorm_hist_dev = nullptr;
     o->refine = 0;
     o->refine_dtype = -1;
+    o->method = PDST_LSQR;
+    o->reserved0 = 0;
     o->refine_tol = 1e-5;
 }
 
@@ -1501,7 +1541,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
     k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, nullptr, ubar, x, wv, partial, sc, sy);
     k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 1);
-    k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, partial, sc, sy);
+    k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
     PDST_CUDA(cudaGetLastError());
     launches += 3;
     for (;;) {
@@ -1511,7 +1551,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
         for (int i = 0; i < kblock; ++i) {
             k_fwd<VT, ST, FMT><<<g_rows, LT, 0, s>>>(a);
             k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 0);
-            k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, partial, sc, sy);
+            k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
         }
         PDST_CUDA(cudaGetLastError());
         launches += 3 * kblock;
@@ -1536,6 +1576,8 @@ extern "C" pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, d
     if (o) opts = *o;
     const int dtype = opts.dtype, fmt = opts.format;
     PDST_CHECK_ARG(dtype >= 0 && dtype <= 2, "pdst_lsqr_noalloc: unknown dtype %d", dtype);
+    PDST_CHECK_ARG(opts.method == PDST_LSQR, "pdst_lsqr_noalloc: LSQR only (method %d)",
+                   opts.method);
     PDST_CHECK_ARG(fmt == PDST_FMT_ELEMENT || fmt == PDST_FMT_BLOCKED,
                    "pdst_lsqr_noalloc: unknown format");
     PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr_noalloc: itmax must be >= 0");

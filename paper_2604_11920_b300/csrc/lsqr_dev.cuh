@@ -116,10 +116,31 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint64_t bytes) 
     }
 }
 
-// G rows of the forward sweep in the blocked layout.  With nz % 4 == 0 each
-// half-warp owns one row (two rows per warp in flight) and each lane whole
-// runs; the next row's run pointers and first cells are prefetched while the
-// current row streams.  Other nz: warp per row, one entry per lane.
+// Paige & Saunders' stopping tests S1-S3 and their machine-precision forms
+// on the current estimates (istop 1-6), itmax (7); SciPy's numbering.
+static __device__ void stop_tests(LsqrScalars *sc) {
+    const double eps = DBL_EPSILON;
+    const double bnorm = sc->bnorm, anorm = sc->anorm, xnorm = sc->xnorm, rnorm = sc->rnorm;
+    const double test1 = rnorm / bnorm;
+    const double test2 = sc->arnorm / (anorm * rnorm + eps);
+    const double test3 = 1.0 / (sc->acond + eps);
+    const double t1s = test1 / (1.0 + anorm * xnorm / bnorm);
+    const double rtol = sc->btol + sc->atol * anorm * xnorm / bnorm;
+    int istop = 0;
+    if (test1 <= rtol) istop = 1;
+    else if (test2 <= sc->atol) istop = 2;
+    else if (test3 <= sc->ctol) istop = 3;
+    else if (1.0 + t1s <= 1.0) istop = 4;
+    else if (1.0 + test2 <= 1.0) istop = 5;
+    else if (1.0 + test3 <= 1.0) istop = 6;
+    else if (sc->itn >= sc->itmax) istop = 7;
+    sc->istop = istop;
+    if (!isfinite(rnorm) || !isfinite(sc->arnorm)) {
+        sc->err = 1;
+        sc->done = 1;
+    }
+}
+
 // One LSQR step of the scalar recurrence (Paige & Saunders 1982): damping
 // rotation, plane rotation, x/w update coefficients, norm estimates and
 // stopping rules.  alpha_new = ||v-bar_{i+1}||, sc->beta = beta_{i+1},
@@ -172,24 +193,112 @@ static __device__ void lsqr_step(LsqrScalars *sc, double alpha_new) {
     sc->itn += 1;
     sc->pending = 1;
     if (sc->hist) sc->hist[sc->itn - 1] = sc->rnorm;
+    stop_tests(sc);
+    if (!isfinite(sc->t1) || !isfinite(sc->t2)) {
+        sc->err = 1;
+        sc->done = 1;
+    }
+}
 
-    const double eps = DBL_EPSILON;
-    const double bnorm = sc->bnorm, anorm = sc->anorm, xnorm = sc->xnorm, rnorm = sc->rnorm;
-    const double test1 = rnorm / bnorm;
-    const double test2 = sc->arnorm / (anorm * rnorm + eps);
-    const double test3 = 1.0 / (sc->acond + eps);
-    const double t1s = test1 / (1.0 + anorm * xnorm / bnorm);
-    const double rtol = sc->btol + sc->atol * anorm * xnorm / bnorm;
-    int istop = 0;
-    if (test1 <= rtol) istop = 1;
-    else if (test2 <= sc->atol) istop = 2;
-    else if (test3 <= sc->ctol) istop = 3;
-    else if (1.0 + t1s <= 1.0) istop = 4;
-    else if (1.0 + test2 <= 1.0) istop = 5;
-    else if (1.0 + test3 <= 1.0) istop = 6;
-    else if (sc->itn >= sc->itmax) istop = 7;
-    sc->istop = istop;
-    if (!isfinite(rnorm) || !isfinite(sc->arnorm) || !isfinite(sc->t1) || !isfinite(sc->t2)) {
+// Givens rotation (c, s, r) of (a, b): r = sqrt(a^2 + b^2) >= 0.
+static __device__ __forceinline__ void givens(double a, double b, double &c, double &s,
+                                              double &r) {
+    r = hypot(a, b);
+    if (r == 0.0) {
+        c = 1.0;
+        s = 0.0;
+    } else {
+        c = a / r;
+        s = b / r;
+    }
+}
+
+// LSMR state after the start step (beta_1 u_1 = b, alpha_1 v_1 = A^T u_1).
+static __device__ void lsmr_init(LsqrScalars *sc, double alpha1) {
+    const double beta1 = sc->beta;
+    sc->alphabar = alpha1;
+    sc->zetabar = alpha1 * beta1;
+    sc->cbar = 1.0;
+    sc->sbar = 0.0;
+    sc->rho_prev = 1.0;
+    sc->rhobar_prev = 1.0;
+    sc->betadd = beta1;
+    sc->betad = 0.0;
+    sc->rhod_prev = 1.0;
+    sc->tautilde_prev = 0.0;
+    sc->thetatilde = 0.0;
+    sc->zeta_prev = 0.0;
+    sc->dsum = 0.0;
+    sc->anorm2 = alpha1 * alpha1;
+    sc->rbar_max = 0.0;
+    sc->rbar_min = DBL_MAX;
+}
+
+// One LSMR step (Fong & Saunders 2011) after the bidiagonalisation produced
+// beta_{k+1} (sc->beta) and alpha_{k+1} (alpha_new): the damping rotation,
+// the rotations P_k and Pbar_k, the coefficients of the vector update
+//   hbar = h - t1 hbar,  x += t2 hbar,  h = v - t3 h,
+// and the estimates: ||A^T r|| = |zetabar_{k+1}|; ||r|| through the rotation
+// Qtilde_{k-1} of (rhodot_{k-1}, thetabar_k) applied to betahat and to R_k y_k
+// (||r||^2 = d + (betadot - taudot)^2 + betadotdot^2, d summing what the
+// damping rotations split off); ||A|| ~ ||B_k||_F; cond(A) ~ max/min rhobar_j.
+// The stopping tests need ||x_k||, so they run after the update (k_upd).
+static __device__ void lsmr_step(LsqrScalars *sc, double alpha_new) {
+    const double beta = sc->beta, lam = sc->damp;
+    if (!(beta > 0.0)) alpha_new = sc->alpha;
+    double chat, shat, alphahat;
+    givens(sc->alphabar, lam, chat, shat, alphahat);
+    double c, s, rho;
+    givens(alphahat, beta, c, s, rho);
+    if (!(rho > 0.0) || !isfinite(rho)) {
+        sc->err = 1;
+        sc->done = 1;
+        return;
+    }
+    const double theta_next = s * alpha_new;
+    sc->alphabar = c * alpha_new;
+    const double thetabar = sc->sbar * rho;
+    double cbar, sbar, rhobar;
+    givens(sc->cbar * rho, theta_next, cbar, sbar, rhobar);
+    const double zeta = cbar * sc->zetabar;
+    sc->zetabar = -sbar * sc->zetabar;
+    sc->cbar = cbar;
+    sc->sbar = sbar;
+    sc->t1 = thetabar * rho / (sc->rho_prev * sc->rhobar_prev);
+    sc->t2 = zeta / (rho * rhobar);
+    sc->t3 = theta_next / rho;
+    // ||r_k||
+    const double betaacute = chat * sc->betadd, betacheck = -shat * sc->betadd;
+    const double betahat = c * betaacute;
+    sc->betadd = -s * betaacute;
+    const double thetatilde_prev = sc->thetatilde;
+    double ctilde, stilde, rhotilde_prev;
+    givens(sc->rhod_prev, thetabar, ctilde, stilde, rhotilde_prev);
+    sc->thetatilde = stilde * rhobar;
+    sc->rhod_prev = ctilde * rhobar;
+    sc->betad = -stilde * sc->betad + ctilde * betahat;
+    sc->tautilde_prev = (sc->zeta_prev - thetatilde_prev * sc->tautilde_prev) / rhotilde_prev;
+    const double taud = (zeta - sc->thetatilde * sc->tautilde_prev) / sc->rhod_prev;
+    sc->dsum += betacheck * betacheck;
+    const double dr = sc->betad - taud;
+    sc->rnorm = sqrt(sc->dsum + dr * dr + sc->betadd * sc->betadd);
+    // ||A||, cond(A), ||A^T r||
+    sc->anorm2 += beta * beta;
+    sc->anorm = sqrt(sc->anorm2);
+    sc->anorm2 += alpha_new * alpha_new;
+    sc->rbar_max = fmax(sc->rbar_max, rhobar);
+    sc->rbar_min = fmin(sc->rbar_min, rhobar);
+    sc->acond = sc->rbar_max / sc->rbar_min;
+    sc->arnorm = fabs(sc->zetabar);
+    sc->rho_prev = rho;
+    sc->rhobar_prev = rhobar;
+    sc->zeta_prev = zeta;
+    sc->alpha = alpha_new;
+    sc->itn += 1;
+    sc->pending = 1;
+    if (sc->hist) sc->hist[sc->itn - 1] = sc->rnorm;
+    if (!isfinite(sc->rnorm) || !isfinite(sc->arnorm) || !isfinite(sc->t1) ||
+        !isfinite(sc->t2) || !isfinite(sc->t3)) {
         sc->err = 1;
         sc->done = 1;
     }

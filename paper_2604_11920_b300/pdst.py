@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libpdst.so")
 F64, F32, BF16, DF64 = 0, 1, 2, 3
 FMT_ELEMENT, FMT_BLOCKED = 0, 1
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
+METHODS = {"lsqr": 0, "lsmr": 1}
 FORMATS = {"element": FMT_ELEMENT, "blocked": FMT_BLOCKED}
 
 STATUS = {0: "PDST_OK", 1: "PDST_ERR_ARG", 2: "PDST_ERR_CUDA", 3: "PDST_ERR_OOM",
@@ -50,7 +51,8 @@ class LsqrOpts(ctypes.Structure):
                 ("kblock", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("rnorm_hist_dev", ctypes.c_void_p),
                 ("refine", ctypes.c_int32), ("refine_dtype", ctypes.c_int32),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("method", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class BatchedOpts(ctypes.Structure):
@@ -157,7 +159,7 @@ def _np_ptr(a: np.ndarray):
 
 def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, precond=0,
               kblock=16, use_graph=True, hist=None, profile=False, refine=0,
-              refine_tol=1e-5, refine_dtype=None) -> LsqrOpts:
+              refine_tol=1e-5, refine_dtype=None, method="lsqr") -> LsqrOpts:
     o = LsqrOpts()
     load().pdst_lsqr_opts_default(ctypes.byref(o))
     o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -170,6 +172,7 @@ def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, prec
                                                       if isinstance(refine_dtype, str)
                                                       else int(refine_dtype))
     o.rnorm_hist_dev = None if hist is None else hist.data_ptr()
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
     return o
 
 
