@@ -76,6 +76,7 @@ def parse_args():
     ap.add_argument("--batched-systems", type=int, default=64)
     ap.add_argument("--only-batched", action="store_true",
                     help="print the batched-workload section alone")
+    ap.add_argument("--no-lsmr", action="store_true", help="skip the LSMR section")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy-matched ladder (large systems)")
     ap.add_argument("--ref-tol", type=float, default=REF_TOL,
@@ -284,16 +285,16 @@ def run_pdst(args, rank, world):
         set_scaling(pc)
         return h.lsqr(d, p.w, p.lam, itmax, tol, dtype=dt, fmt=fm, precond=1 if pc else 0, **kw)
 
-    def timed(form, steps, warmup):
+    def timed(form, steps, warmup, **kw):
         for _ in range(warmup):
-            solve(form)
+            solve(form, **kw)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         e0.record(stream)
         for _ in range(steps):
-            r = solve(form)
+            r = solve(form, **kw)
             launches += r.info["kernel_launches"]
         e1.record(stream)
         torch.cuda.synchronize()
@@ -373,6 +374,18 @@ def run_pdst(args, rank, world):
                             "speedup": (acc_plain["s"] / acc_chosen["s"])
                             if acc_plain["s"] and acc_chosen["s"] else None}
 
+    # LSMR (the paper's solver) on the same sweeps: chosen form and plain FP64
+    lsmr_sec = None
+    if not args.no_lsmr:
+        ms_l, res_l, _ = timed(args.form, max(1, min(args.steps, 3)), 1, method="lsmr")
+        ms_lp, res_lp, _ = timed(PLAIN, 1, 1, method="lsmr")
+        lsmr_sec = {"chosen": {"s": ms_l / 1e3, "iters": res_l.info["iters"],
+                               "istop": res_l.info["istop"],
+                               "model_error_vs_fp64_ref": relerr(res_l.m)},
+                    "plain_fp64": {"s": ms_lp / 1e3, "iters": res_lp.info["iters"],
+                                   "model_error_vs_fp64_ref": relerr(res_lp.m)},
+                    "speedup_vs_plain_fp64": ms_lp / ms_l}
+
     # per-kernel device time (events around each launch, same solve)
     prof = solve(args.form, profile=True)
     pi = max(prof.info["profiled_iters"], 1)
@@ -435,6 +448,7 @@ def run_pdst(args, rank, world):
                        "model_error_vs_fp64_ref": relerr(m_plain)},
         "speedup_vs_plain_fp64": ms_plain / ms,
         "accuracy_matched": accuracy_matched,
+        "lsmr": lsmr_sec,
         "kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
         "spmv_gbs": spmv_gbs,
         "build_G_s": build_s,
