@@ -77,6 +77,7 @@ def parse_args():
     ap.add_argument("--only-batched", action="store_true",
                     help="print the batched-workload section alone")
     ap.add_argument("--no-lsmr", action="store_true", help="skip the LSMR section")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the damping-sweep section")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy-matched ladder (large systems)")
     ap.add_argument("--ref-tol", type=float, default=REF_TOL,
@@ -386,6 +387,25 @@ def run_pdst(args, rank, world):
                                    "model_error_vs_fp64_ref": relerr(res_lp.m)},
                     "speedup_vs_plain_fp64": ms_lp / ms_l}
 
+    # damping sweep: 8 damping values from one bidiagonalisation vs 8 solves
+    sweep_sec = None
+    if not args.no_sweep:
+        lams = [float(10.0 ** (-3 + 3 * i / 7)) for i in range(8)]   # logspace(-3, 0, 8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sw = h.lsqr_damping_sweep(d, p.w, lams, itmax, p.tol, dtype="f32", fmt="blocked")
+        torch.cuda.synchronize()
+        t_sweep = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sep = [h.lsqr(d, p.w, lm, itmax, p.tol, dtype="f32", fmt="blocked") for lm in lams]
+        torch.cuda.synchronize()
+        t_sep = time.perf_counter() - t0
+        sweep_sec = {"lambdas": lams, "form": "f32-blocked (no scaling)",
+                     "sweep_s": t_sweep, "separate_s": t_sep, "speedup": t_sep / t_sweep,
+                     "iters": [r.info["iters"] for r in sw],
+                     "identical_to_separate": all(
+                         bool(torch.equal(a.m, b.m)) for a, b in zip(sw, sep))}
+
     # per-kernel device time (events around each launch, same solve)
     prof = solve(args.form, profile=True)
     pi = max(prof.info["profiled_iters"], 1)
@@ -449,6 +469,7 @@ def run_pdst(args, rank, world):
         "speedup_vs_plain_fp64": ms_plain / ms,
         "accuracy_matched": accuracy_matched,
         "lsmr": lsmr_sec,
+        "damping_sweep": sweep_sec,
         "kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
         "spmv_gbs": spmv_gbs,
         "build_G_s": build_s,

@@ -243,6 +243,26 @@ pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, double w, do
                               int32_t itmax, double tol, double *m_out_dev,
                               pdst_lsqr_info *info, const pdst_lsqr_opts *opts, void *stream);
 
+/* Damping sweep (no counterpart in the paper's solver module): the solutions of
+ *     min_m ||G m - d||^2 + w^2 ||L m||^2 + lambda_l^2 ||m||^2,   l = 0..nlam-1,
+ * from ONE Golub-Kahan bidiagonalisation of A = [G; w L].  The vectors u, v
+ * (and alpha, beta) of LSQR do not depend on the damping, which enters only
+ * the scalar recurrence (Paige & Saunders 1982), so each damping value costs
+ * one recurrence and one x/w update per iteration instead of a full solve.
+ * Every value stops on its own tests (atol = btol = tol unless opts set them);
+ * the sweeps run until all have stopped or itmax.  Results are identical to
+ * nlam separate pdst_lsqr calls with the same options.
+ *   lambda_host  nlam damping values (host, copied), 1 <= nlam <= 64
+ *   m_out_dev    nlam caller-owned device arrays of n doubles
+ *   infos        nlam entries (iters, istop and estimates per value), or NULL
+ *   opts         dtype / format / kblock / atol / btol / conlim as pdst_lsqr;
+ *                precond, refine, profile must be 0 and method PDST_LSQR
+ * Errors as pdst_lsqr.  Synchronous on return. */
+pdst_status pdst_lsqr_damping_sweep(pdst_handle_t h, const double *d_dev, double w, int32_t nlam,
+                                    const double *lambda_host, int32_t itmax, double tol,
+                                    double *const *m_out_dev, pdst_lsqr_info *infos,
+                                    const pdst_lsqr_opts *opts, void *stream);
+
 /* Same as pdst_lsqr with host d and m (pinned or pageable): copies d in and
  * m out inside the call (the end-to-end path). */
 pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w, double lambda,

@@ -31,7 +31,8 @@ namespace {
 constexpr int BT = 256;      // threads per block
 constexpr int RMAX = 16;     // right-hand sides per system (lanes of a half-warp)
 constexpr int LCOLS = 32;    // columns per stencil / update work item
-constexpr int NB = 6;        // work buffers per system: U, V, X, W, chunk sums, chunk counters
+constexpr int NB = 7;        // work buffers per system: U, V, X, W, chunk sums, chunk counters,
+                             // cell sums
 
 template <class VT, class ST> struct BSys {
     int64_t m;
@@ -51,6 +52,7 @@ template <class VT, class ST> struct BSys {
     int32_t adj_chunk;         // rows per adjoint work item
     ST *chunk_part;   // adjoint work items x nz x RMAX partial sums
     unsigned *cell_done;       // H finished-chunk counters
+    double *cell_ss;           // H x RMAX: sum of v^2 of cells finished across several items
     ST *U;            // (m + n) x RS, right-hand side fastest (padding lanes stay 0)
     ST *V;            // n x RS, right-hand side fastest (padding lanes stay 0)
     double *X, *W;    // n x R
@@ -514,6 +516,15 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
     for (int b = 0; b < 4; ++b) q[b] = __shfl_sync(FULL, ss4[b], j >> 2);
     const int cpt = j & 3;
     const double r = cpt == 0 ? q[0] : cpt == 1 ? q[1] : cpt == 2 ? q[2] : q[3];
+    if (nch > 1) {
+        // the finishing item depends on arrival order: the cell's sums go to
+        // its slots, added in cell order by k_bred
+        if (finish && lane < 16) {
+            S.cell_ss[(int64_t)h * RMAX + j] = r;
+            __threadfence();
+        }
+        return 0.0;
+    }
     return lane < 16 ? r : 0.0;
 }
 
@@ -604,6 +615,13 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
             ss += (double)v * (double)v;
         }
     }
+    if (nch > 1) {
+        if (finish && half == 0 && j < R) {
+            S.cell_ss[(int64_t)h * RMAX + j] = ss;
+            __threadfence();
+        }
+        return 0.0;
+    }
     return ss;
 }
 
@@ -692,6 +710,10 @@ __global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, int G, const 
     BSys<VT, ST> &S = sys[s];
     double acc = 0.0;
     for (int b = l; b < G; b += RED_T / RMAX) acc += partial[((int64_t)s * G + b) * RMAX + j];
+    if (phase == PH_ADJ_INIT || phase == PH_ADJ) {
+        const int H = S.n / S.nz;
+        for (int hh = l; hh < H; hh += RED_T / RMAX) acc += __ldcg(S.cell_ss + (int64_t)hh * RMAX + j);
+    }
     part[l][j] = acc;
     __syncthreads();
     if (t < RMAX && j < S.R) {
@@ -838,8 +860,11 @@ template <class VT, class ST> struct Batched {
                 pdst_handle *h = hs[i];
                 const int R = nrhs[i];
                 DevBuf *U = new DevBuf, *V = new DevBuf, *X = new DevBuf, *W = new DevBuf;
-                DevBuf *CP = new DevBuf, *CD = new DevBuf;
-                bw->bufs.insert(bw->bufs.end(), {U, V, X, W, CP, CD});
+                DevBuf *CP = new DevBuf, *CD = new DevBuf, *CS = new DevBuf;
+                bw->bufs.insert(bw->bufs.end(), {U, V, X, W, CP, CD, CS});
+                const int64_t csb = sizeof(double) * std::max<int64_t>((int64_t)h->H * RMAX, 1);
+                PDST_TRY(CS->alloc(csb));
+                PDST_CUDA(cudaMemsetAsync(CS->p, 0, csb, s));
                 PDST_TRY(CP->alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz * RMAX, 1)));
                 PDST_TRY(CD->alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
                 PDST_CUDA(cudaMemsetAsync(CD->p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
@@ -888,6 +913,7 @@ template <class VT, class ST> struct Batched {
             q.W = bw->bufs[NB * i + 3]->as<double>();
             q.chunk_part = bw->bufs[NB * i + 4]->as<ST>();
             q.cell_done = bw->bufs[NB * i + 5]->as<unsigned>();
+            q.cell_ss = bw->bufs[NB * i + 6]->as<double>();
             q.adj_item = h->adj_item.as<int32_t>();
             q.adj_chunk = h->adj_chunk;
             q.sc = scd + (size_t)i * RMAX;

@@ -50,6 +50,10 @@ template <class VT, class ST> struct OpArgs {
     const VT *valT;           // element CSC order (element layout only)
     const VT *valB;           // blocked CSC order
     double *hbar;             // LSMR h-bar (n)
+    LsqrScalars *lam_sc;      // damping sweep: one recurrence per damping value
+    double *cell_ss;          // H: sum of v-bar^2 over a cell split over several items
+    int32_t n_cells;          // H
+    int32_t n_lam;            // 0: ordinary solve
     const int32_t *adj_item;  // (cell, first row) per adjoint work item
     int32_t adj_chunk;        // rows per adjoint work item
     int64_t n_adj;
@@ -476,11 +480,23 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
             }
         }
         if (finish) {
+            double css = 0.0;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int k = lane + 32 * half;
                 if (k < nz)
-                    ss += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr, init);
+                    css += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr, init);
+            }
+            if (nch > 1) {
+                // which item finishes the cell depends on arrival order: its
+                // sum goes to the cell's slot, added in cell order at the end
+                css = warp_sum(css);
+                if (lane == 0) {
+                    a.cell_ss[h] = css;
+                    __threadfence();
+                }
+            } else {
+                ss += css;
             }
         }
     }
@@ -519,6 +535,22 @@ __device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigne
     if (threadIdx.x == 0) *counter = 0u;
     total = s;
     return true;
+}
+
+// Sum of v[0..n) by the calling block in a fixed order (thread t takes
+// t, t + blockDim, ...; then warps in order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum_ordered(const double *v, int64_t n) {
+    __shared__ double red2[LT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(v + i);
+    s = warp_sum(s);
+    if (lane == 0) red2[warp] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red2[i];
+    return t;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -608,6 +640,39 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_fwd(OpArgs<VT, 
     }
 }
 
+// Damping sweep: u and v (and so alpha and beta) do not depend on the
+// damping, which enters only the scalar recurrence.  After alpha_{k+1} is
+// known, advance the recurrence of every damping value still running; the
+// bidiagonalisation stops (base istop) once all have stopped.
+static __device__ void sweep_step(LsqrScalars *base, LsqrScalars *ls, int L, double an, int init) {
+    int running = 0;
+    for (int l = 0; l < L; ++l) {
+        LsqrScalars *c = ls + l;
+        if (init) {
+            c->beta = base->beta;
+            c->bnorm = base->bnorm;
+            c->rnorm = base->rnorm;
+            c->phibar = base->phibar;
+            c->alpha = an;
+            c->rhobar = an;
+            c->arnorm = an * base->beta;
+            c->pending = 2;
+            if (!(c->arnorm > 0.0)) c->done = 1;
+        } else if (!(c->done | c->istop)) {
+            c->beta = base->beta;
+            lsqr_step(c, an);
+        }
+        if (c->err) base->err = 1;
+        running += !(c->done | c->istop);
+    }
+    base->alpha = an;
+    if (!init) base->itn += 1;
+    if (!running) {
+        if (init) base->done = 1;
+        else base->istop = 1;
+    }
+}
+
 // v-bar <- (A^T u-bar)/beta - (beta/alpha) v-bar;  alpha <- ||v-bar||, then
 // the scalar recurrence (or its initialisation when init != 0).  With BF16
 // values three blocks per SM (up to 85 registers) measured faster than four.
@@ -638,14 +703,21 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
         }
     }
     double tot;
-    if (grid_sum_last(ss, a.partial + MAXBLK, &a.sy->count[2], tot) && threadIdx.x == 0) {
+    const bool last = grid_sum_last(ss, a.partial + MAXBLK, &a.sy->count[2], tot);
+    if (!last) return;
+    // cells finished across several items, in cell order
+    const double cells = (FMT == FMT_BLK && !skip) ? block_sum_ordered(a.cell_ss, a.n_cells) : 0.0;
+    if (threadIdx.x == 0) {
+        tot += cells;
         double an = skip ? alpha : sqrt(tot);
         if (!isfinite(an)) {
             sc->err = 1;
             sc->done = 1;
             return;
         }
-        if (init) {
+        if (a.n_lam > 0) {
+            sweep_step(sc, a.lam_sc, a.n_lam, an, init);
+        } else if (init) {
             sc->alpha = an;
             sc->rhobar = an;
             sc->arnorm = an * beta;
@@ -657,6 +729,20 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
         } else {
             lsqr_step(sc, an);
         }
+    }
+}
+
+// The LSQR update of one column with fixed rounding (explicit round-to-nearest
+// operations, so that every kernel that applies it gives the same bits):
+// v = v-bar / alpha; start step: w = v; otherwise x += t1 w, w = v + t2 w.
+__device__ __forceinline__ void lsqr_xw(double vbar_j, double ia, double t1, double t2, int pend,
+                                        double &x, double &w) {
+    const double v = __dmul_rn(vbar_j, ia);
+    if (pend == 2) {
+        w = v;
+    } else {
+        x = __fma_rn(t1, w, x);
+        w = __fma_rn(t2, w, v);
     }
 }
 
@@ -702,19 +788,44 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
     }
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)vbar[j] * ia;
-        double w = wv[j];
-        if (pend == 2) {
-            w = v;
-        } else {
-            x[j] += t1 * w;
-            w = v + t2 * w;
-        }
+        double w = wv[j], xj = x[j];
+        lsqr_xw((double)vbar[j], ia, t1, t2, pend, xj, w);
+        if (pend != 2) x[j] = xj;
         wv[j] = w;
-        ss += w * w;
+        ss = __fma_rn(w, w, ss);
     }
     double tot;
     if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot) && threadIdx.x == 0) {
+        sc->wnorm2 = tot;
+        sc->pending = 0;
+    }
+}
+
+// Damping sweep, y-slice l of the grid: x_l += t1 w_l; w_l = v + t2 w_l with
+// damping value l's coefficients; ||w_l||^2 to its recurrence.
+template <class ST>
+__global__ void __launch_bounds__(LT) k_upd_sweep(int32_t n, const ST *__restrict__ vbar, double *X,
+                                                  double *W, double *partial, LsqrScalars *ls,
+                                                  unsigned *counters) {
+    const int l = blockIdx.y;
+    LsqrScalars *sc = ls + l;
+    const int pend = sc->pending;
+    if (!pend) return;
+    const double alpha = sc->alpha;
+    const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    const double t1 = sc->t1, t2 = sc->t2;
+    double *x = X + (int64_t)l * n, *wv = W + (int64_t)l * n;
+    double ss = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double w = wv[j], xj = x[j];
+        lsqr_xw((double)vbar[j], ia, t1, t2, pend, xj, w);
+        if (pend != 2) x[j] = xj;
+        wv[j] = w;
+        ss = __fma_rn(w, w, ss);
+    }
+    double tot;
+    if (grid_sum_last(ss, partial + (int64_t)l * MAXBLK, counters + l, tot) && threadIdx.x == 0) {
         sc->wnorm2 = tot;
         sc->pending = 0;
     }
@@ -790,8 +901,9 @@ struct LsqrWork {
     int dtype = -1, format = -1, lamrows = -1;
     const void *graph_D = nullptr;
     int64_t M = 0;
-    DevBuf ubar, vbar, vsc, x, wv, hbar, partial, scal, sync, chunk_part, cell_done;
+    DevBuf ubar, vbar, vsc, x, wv, hbar, partial, scal, sync, chunk_part, cell_done, cell_ss;
     DevBuf ones, baug, corr;         // refinement: unit scaling, augmented residual, norms
+    DevBuf sw_x, sw_w, sw_sc, sw_part, sw_cnt;   // damping sweep: x, w, scalars per value
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
     std::map<int, cudaGraphExec_t> graphs;   // key: kblock
@@ -827,6 +939,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     a.valB = h->vals[dtype].bcsc.as<VT>();
     a.adj_item = h->adj_item.as<int32_t>();
     a.adj_chunk = h->adj_chunk;
+    a.n_cells = h->H;
     a.n_adj = h->n_adj;
     a.D = scaled ? h->colscale.as<double>() : nullptr;
     a.lam_rows_on = lamrows ? 1 : 0;
@@ -842,6 +955,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
         a.sy = w->sync.as<LsqrSync>();
         a.chunk_part = w->chunk_part.as<ST>();
         a.cell_done = w->cell_done.as<unsigned>();
+        a.cell_ss = w->cell_ss.as<double>();
     }
     return a;
 }
@@ -864,6 +978,9 @@ struct RunStats {
 };
 
 template <class VT, class ST, int FMT> struct Solver {
+    using VTy = VT;
+    using STy = ST;
+    static constexpr int FMTv = FMT;
     static pdst_status prepare(pdst_handle *h, LsqrWork *w, bool lamrows) {
         const int64_t M = h->m + h->n + (lamrows ? h->n : 0);
         PDST_TRY(w->ubar.alloc(sizeof(ST) * std::max<int64_t>(M, 1)));
@@ -877,6 +994,8 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_TRY(w->sync.alloc(sizeof(LsqrSync)));
         PDST_TRY(w->chunk_part.alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz, 1)));
         PDST_TRY(w->cell_done.alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
+        PDST_TRY(w->cell_ss.alloc(sizeof(double) * std::max<int32_t>(h->H, 1)));
+        PDST_CUDA(cudaMemset(w->cell_ss.p, 0, sizeof(double) * std::max<int32_t>(h->H, 1)));
         if (!w->h_scal) PDST_CUDA(cudaMallocHost(&w->h_scal, sizeof(LsqrScalars)));
         w->M = M;
         // warp-per-row kernels: items = rows * 32 threads
@@ -1351,6 +1470,194 @@ static pdst_status colnorm_scaling(pdst_handle *h, double w, double lam, double 
     return PDST_OK;
 }
 
+// ------------------------------------------------------------ damping sweep
+
+constexpr int MAX_SWEEP = 64;
+
+template <class VT, class ST, int FMT>
+static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const double *d,
+                             const LsqrScalars &base0, std::vector<LsqrScalars> &lam,
+                             int kblock, double *const *m_out, cudaStream_t s, int &launches) {
+    const int L = (int)lam.size();
+    const int64_t n = h->n;
+    PDST_TRY(w->sw_x.alloc(sizeof(double) * std::max<int64_t>(L * n, 1)));
+    PDST_TRY(w->sw_w.alloc(sizeof(double) * std::max<int64_t>(L * n, 1)));
+    PDST_TRY(w->sw_sc.alloc(sizeof(LsqrScalars) * L));
+    PDST_TRY(w->sw_part.alloc(sizeof(double) * L * MAXBLK));
+    PDST_TRY(w->sw_cnt.alloc(sizeof(unsigned) * L));
+    OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, false, false);
+    a.lam_sc = w->sw_sc.as<LsqrScalars>();
+    a.n_lam = L;
+    double *X = w->sw_x.as<double>(), *W = w->sw_w.as<double>();
+    PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
+    PDST_CUDA(cudaMemsetAsync(w->cell_done.p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
+    PDST_CUDA(cudaMemsetAsync(w->sw_cnt.p, 0, sizeof(unsigned) * L, s));
+    PDST_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * L * n, s));
+    *w->h_scal = base0;
+    PDST_CUDA(cudaMemcpyAsync(w->scal.p, w->h_scal, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
+    PDST_CUDA(cudaMemcpyAsync(w->sw_sc.p, lam.data(), sizeof(LsqrScalars) * L,
+                              cudaMemcpyHostToDevice, s));
+    const dim3 gu(w->grid_vec, L);
+    const unsigned ginit = persistent_grid(k_init<ST>, h->device, w->M);
+    k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, nullptr, a.ubar, a.x, a.wv, a.partial,
+                                    a.sc, a.sy);
+    k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
+    k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.lam_sc,
+                                      w->sw_cnt.as<unsigned>());
+    PDST_CUDA(cudaGetLastError());
+    launches += 3;
+    for (;;) {
+        PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
+                                  cudaMemcpyDeviceToHost, s));
+        PDST_CUDA(cudaStreamSynchronize(s));
+        const LsqrScalars &c = *w->h_scal;
+        if (c.done || c.istop || c.err || c.itn >= c.itmax) break;
+        for (int i = 0; i < kblock; ++i) {
+            k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
+            k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+            k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(),
+                                              a.lam_sc, w->sw_cnt.as<unsigned>());
+        }
+        PDST_CUDA(cudaGetLastError());
+        launches += 3 * kblock;
+    }
+    for (int l = 0; l < L; ++l)
+        k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, X + (int64_t)l * n, nullptr, m_out[l], 0);
+    PDST_CUDA(cudaGetLastError());
+    launches += L;
+    PDST_CUDA(cudaMemcpyAsync(lam.data(), w->sw_sc.p, sizeof(LsqrScalars) * L,
+                              cudaMemcpyDeviceToHost, s));
+    PDST_CUDA(cudaStreamSynchronize(s));
+    return PDST_OK;
+}
+
+static pdst_status sweep_impl(pdst_handle *h, const double *d_dev, double w_s, int32_t nlam,
+                              const double *lambda_host, int32_t itmax, double tol,
+                              double *const *m_out, pdst_lsqr_info *infos,
+                              const pdst_lsqr_opts *o, cudaStream_t s) {
+    pdst_lsqr_opts opts;
+    pdst_lsqr_opts_default(&opts);
+    if (o) opts = *o;
+    const int dtype = opts.dtype, fmt = opts.format;
+    PDST_CHECK_ARG(nlam >= 1 && nlam <= MAX_SWEEP, "pdst_lsqr_damping_sweep: nlam must be in 1..%d",
+                   MAX_SWEEP);
+    PDST_CHECK_ARG(lambda_host && m_out, "pdst_lsqr_damping_sweep: NULL lambda or m_out");
+    for (int l = 0; l < nlam; ++l) {
+        PDST_CHECK_ARG(std::isfinite(lambda_host[l]) && lambda_host[l] >= 0.0,
+                       "pdst_lsqr_damping_sweep: lambda[%d] must be finite and >= 0", l);
+        PDST_CHECK_ARG(m_out[l], "pdst_lsqr_damping_sweep: m_out[%d] is NULL", l);
+    }
+    PDST_CHECK_ARG(dtype >= 0 && dtype <= 3, "pdst_lsqr_damping_sweep: unknown dtype %d", dtype);
+    PDST_CHECK_ARG(fmt == PDST_FMT_ELEMENT || fmt == PDST_FMT_BLOCKED,
+                   "pdst_lsqr_damping_sweep: unknown format");
+    PDST_CHECK_ARG(itmax >= 0, "pdst_lsqr_damping_sweep: itmax must be >= 0");
+    PDST_CHECK_ARG(std::isfinite(w_s) && w_s >= 0.0, "pdst_lsqr_damping_sweep: bad w");
+    PDST_CHECK_ARG(std::isfinite(tol) && tol >= 0.0, "pdst_lsqr_damping_sweep: bad tol");
+    PDST_CHECK_ARG(h->m == 0 || d_dev, "pdst_lsqr_damping_sweep: d is NULL");
+    PDST_CHECK_ARG(opts.precond == 0 && opts.refine == 0 && opts.profile == 0 &&
+                       opts.method == PDST_LSQR,
+                   "pdst_lsqr_damping_sweep: plain LSQR only (no scaling, refinement, profile "
+                   "or LSMR)");
+    if (!h->vals[dtype].present) {
+        set_error("pdst_lsqr_damping_sweep: values of dtype %d were not kept", dtype);
+        return PDST_ERR_STATE;
+    }
+    if (dtype == PDST_DF64 && fmt != PDST_FMT_BLOCKED) {
+        set_error("pdst_lsqr_damping_sweep: the double-float form runs on the blocked layout only");
+        return PDST_ERR_ARG;
+    }
+    if (fmt == PDST_FMT_ELEMENT && !(h->formats & (1u << PDST_FMT_ELEMENT))) {
+        set_error("pdst_lsqr_damping_sweep: element indices were not built");
+        return PDST_ERR_STATE;
+    }
+    if (fmt == PDST_FMT_BLOCKED && !blocked_nz_ok(h->nz)) {
+        set_error("pdst_lsqr_damping_sweep: the blocked layout needs nz <= 64");
+        return PDST_ERR_LIMIT;
+    }
+    const int kblock = opts.kblock > 0 ? opts.kblock : 16;
+    LsqrScalars base{};
+    base.cs2 = -1.0;
+    base.itmax = itmax;
+    base.w_smooth = w_s;
+    std::vector<LsqrScalars> lam(nlam);
+    for (int l = 0; l < nlam; ++l) {
+        LsqrScalars &c = lam[l];
+        c = LsqrScalars{};
+        c.cs2 = -1.0;
+        c.damp = lambda_host[l];
+        c.atol = opts.atol >= 0.0 ? opts.atol : tol;
+        c.btol = opts.btol >= 0.0 ? opts.btol : tol;
+        c.ctol = 1.0 / (opts.conlim > 0.0 ? opts.conlim : 1e8);
+        c.w_smooth = w_s;
+        c.itmax = itmax;
+    }
+    if (itmax == 0) {
+        for (int l = 0; l < nlam; ++l) PDST_CUDA(cudaMemsetAsync(m_out[l], 0, sizeof(double) * h->n, s));
+        if (infos)
+            for (int l = 0; l < nlam; ++l) infos[l] = pdst_lsqr_info{};
+        PDST_CUDA(cudaStreamSynchronize(s));
+        return PDST_OK;
+    }
+    if (!h->work) h->work = new LsqrWork();
+    LsqrWork *w = h->work;
+    const bool fresh = w->dtype != dtype || w->format != fmt || w->lamrows != 0;
+    if (fresh) {
+        // buffers may move: the ordinary solve's captured graphs are stale
+        for (auto &g : w->graphs)
+            if (g.second) cudaGraphExecDestroy(g.second);
+        w->graphs.clear();
+    }
+    int launches = 0;
+    pdst_status st;
+    auto prep_run = [&](auto tag) -> pdst_status {
+        using S = decltype(tag);
+        if (fresh) PDST_TRY((S::prepare(h, w, false)));
+        return sweep_run<typename S::VTy, typename S::STy, S::FMTv>(h, w, dtype, d_dev, base, lam,
+                                                                   kblock, m_out, s, launches);
+    };
+    if (dtype == PDST_DF64)
+        st = prep_run(Solver<dfl, dfl, FMT_BLK>{});
+    else if (dtype == PDST_F64)
+        st = fmt == PDST_FMT_ELEMENT ? prep_run(Solver<double, double, FMT_ELEM>{})
+                                     : prep_run(Solver<double, double, FMT_BLK>{});
+    else if (dtype == PDST_F32)
+        st = fmt == PDST_FMT_ELEMENT ? prep_run(Solver<float, float, FMT_ELEM>{})
+                                     : prep_run(Solver<float, float, FMT_BLK>{});
+    else
+        st = fmt == PDST_FMT_ELEMENT ? prep_run(Solver<__nv_bfloat16, float, FMT_ELEM>{})
+                                     : prep_run(Solver<__nv_bfloat16, float, FMT_BLK>{});
+    if (st != PDST_OK) {
+        w->dtype = -1;
+        return st;
+    }
+    w->dtype = dtype;
+    w->format = fmt;
+    w->lamrows = 0;
+    bool err = w->h_scal->err != 0;
+    for (int l = 0; l < nlam; ++l) {
+        const LsqrScalars &c = lam[l];
+        err |= c.err != 0;
+        if (infos) {
+            pdst_lsqr_info &f = infos[l];
+            f = pdst_lsqr_info{};
+            f.iters = c.itn;
+            f.istop = c.istop;
+            f.rnorm = c.rnorm;
+            f.arnorm = c.arnorm;
+            f.anorm = c.anorm;
+            f.acond = c.acond;
+            f.xnorm = c.xnorm;
+            f.bnorm = c.bnorm;
+            f.kernel_launches = launches;
+        }
+    }
+    if (err) {
+        set_error("pdst_lsqr_damping_sweep: non-finite value in a recurrence");
+        return PDST_ERR_BREAKDOWN;
+    }
+    return PDST_OK;
+}
+
 }  // namespace pdst
 
 using namespace pdst;
@@ -1380,6 +1687,16 @@ extern "C" pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w,
     PDST_CHECK_ARG(h != nullptr, "pdst_lsqr: handle is NULL");
     return lsqr_impl(h, d_dev, w, lambda, itmax, tol, m_out_dev, info, opts,
                      (cudaStream_t)stream);
+}
+
+extern "C" pdst_status pdst_lsqr_damping_sweep(pdst_handle_t h, const double *d_dev, double w,
+                                               int32_t nlam, const double *lambda_host,
+                                               int32_t itmax, double tol,
+                                               double *const *m_out_dev, pdst_lsqr_info *infos,
+                                               const pdst_lsqr_opts *opts, void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_lsqr_damping_sweep: handle is NULL");
+    return sweep_impl(h, d_dev, w, nlam, lambda_host, itmax, tol, m_out_dev, infos, opts,
+                      (cudaStream_t)stream);
 }
 
 extern "C" pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w,
@@ -1502,7 +1819,7 @@ static size_t noalloc_need(int64_t M, int64_t n, size_t st, int64_t chunk_vals, 
     return align256(sizeof(LsqrScalars)) + align256(sizeof(LsqrSync)) +
            align256(sizeof(double) * 3 * MAXBLK) + align256(st * M) + 2 * align256(st * n) +
            2 * align256(sizeof(double) * n) + align256(st * chunk_vals) +
-           align256(sizeof(unsigned) * H);
+           align256(sizeof(unsigned) * H) + align256(sizeof(double) * H);
 }
 
 template <class VT, class ST, int FMT>
@@ -1527,10 +1844,12 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     auto *wv = reinterpret_cast<double *>(carve(sizeof(double) * h->n));
     auto *cpart = reinterpret_cast<ST *>(carve(sizeof(ST) * h->n_adj * h->nz));
     auto *cdone = reinterpret_cast<unsigned *>(carve(sizeof(unsigned) * h->H));
+    auto *css = reinterpret_cast<double *>(carve(sizeof(double) * h->H));
 
     OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, nullptr, scaled, lamrows);
     a.chunk_part = cpart;
     a.cell_done = cdone;
+    a.cell_ss = css;
     a.ubar = ubar;
     a.vbar = vbar;
     a.vsc = scaled ? vsc : vbar;
@@ -1549,6 +1868,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     // before it is read (k_init, the start step of k_adj, k_upd)
     PDST_CUDA(cudaMemsetAsync(sy, 0, sizeof(LsqrSync), s));
     PDST_CUDA(cudaMemsetAsync(cdone, 0, sizeof(unsigned) * h->H, s));
+    PDST_CUDA(cudaMemsetAsync(css, 0, sizeof(double) * h->H, s));
     LsqrScalars hs = init;
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
     k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, nullptr, ubar, x, wv, partial, sc, sy);

@@ -94,6 +94,8 @@ SIGNATURES = {
                          ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_lsqr_host": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
                               ctypes.POINTER(LsqrOpts), _vp]),
+    "pdst_lsqr_damping_sweep": (_i32, [_vp, _vp, _d, _i32, _vp, _i32, _d, _vp,
+                                       ctypes.POINTER(LsqrInfo), ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_lsqr_noalloc": (_i32, [_vp, _vp, _d, _d, _i32, _d, _vp, ctypes.POINTER(LsqrInfo),
                                  ctypes.POINTER(LsqrOpts), _vp]),
     "pdst_set_col_scaling": (_i32, [_vp, _vp, _d, _d, _vp]),
@@ -248,6 +250,21 @@ class Handle:
                                 int(itmax), tol, _dev_ptr(m_out, self.n, torch.float64, "m_out"),
                                 ctypes.byref(info), ctypes.byref(o), _stream(stream)))
         return Result(m_out, info.as_dict())
+
+    def lsqr_damping_sweep(self, d, w, lambdas, itmax, tol, stream=None, **opt_kw):
+        """Solutions for several damping values from one bidiagonalisation:
+        a list of Result, one per value of `lambdas`."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        L = lam.shape[0]
+        outs = [torch.empty(self.n, dtype=torch.float64, device=d.device) for _ in range(L)]
+        ptrs = (ctypes.c_void_p * L)(*[o.data_ptr() for o in outs])
+        infos = (LsqrInfo * L)()
+        o = lsqr_opts(**opt_kw)
+        _check(load().pdst_lsqr_damping_sweep(
+            self.ptr, _dev_ptr(d, self.m, torch.float64, "d"), float(w), L, _np_ptr(lam),
+            int(itmax), float(tol), ptrs, infos, ctypes.byref(o), _stream(stream)))
+        return [Result(outs[i], infos[i].as_dict()) for i in range(L)]
 
     def lsqr_noalloc(self, d, w, lam, itmax, tol, m_out, stream=None, **opt_kw) -> Result:
         """pdst_lsqr_noalloc: the same solve with no device allocation (the
