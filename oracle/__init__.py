@@ -55,7 +55,8 @@ def _load():
                                        ctypes.c_int64, _d, _i32]
         lib.oracle_G_count.restype = ctypes.c_int
         lib.oracle_G_fill.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_int64, _d, _i32, _d, _i64, _i32, _d]
+                                      ctypes.c_int64, _d, _i32, _d, _d, ctypes.c_int, _i64,
+                                      _i32, _d]
         lib.oracle_G_fill.restype = ctypes.c_int
         lib.oracle_transpose.argtypes = [ctypes.c_int64, ctypes.c_int32, _i64, _i32, _d,
                                          _i64, _i32, _d]
@@ -118,8 +119,9 @@ class CSR:
 
 
 def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
-            row_period: np.ndarray, kdz: np.ndarray) -> CSR:
-    """Sensitivity matrix G (rows = paths in the order given) as CSR."""
+            row_period: np.ndarray, kdz: np.ndarray, kdz_cells=None) -> CSR:
+    """Sensitivity matrix G (rows = paths in the order given) as CSR; with
+    kdz_cells (nx*ny, periods, nz) a depth kernel per horizontal cell."""
     lib = _load()
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 6)
     row_period = np.ascontiguousarray(row_period, dtype=np.int32)
@@ -137,14 +139,21 @@ def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
     nnz = int(ptr[-1])
     col = np.zeros(nnz, dtype=np.int32)
     val = np.zeros(nnz, dtype=np.float64)
+    kc = None
+    if kdz_cells is not None:
+        kc = np.ascontiguousarray(kdz_cells, dtype=np.float64)
+        if kc.shape != (nx * ny, kdz.shape[0], nz):
+            raise ValueError("kdz_cells must be (nx*ny, periods, nz)")
     if lib.oracle_G_fill(nx, ny, nz, dx_km, m, _p(ctrl, _d), _p(row_period, _i32), _p(kdz, _d),
-                         _p(ptr, _i64), _p(col, _i32), _p(val, _d)) != 0:
+                         _p(kc, _d), int(kdz.shape[0]), _p(ptr, _i64), _p(col, _i32),
+                         _p(val, _d)) != 0:
         raise MemoryError("oracle_G_fill")
     return CSR(ptr, col, val, nx * ny * nz)
 
 
 def build_G_problem(p) -> CSR:
-    return build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, p.kdz)
+    return build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, p.kdz,
+                   getattr(p, "kdz_cells", None))
 
 
 def transpose(G: CSR) -> CSR:

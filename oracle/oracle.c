@@ -153,9 +153,14 @@ int oracle_G_count(int nx, int ny, double dx, int64_t n_rows, const double *ctrl
     return rc;
 }
 
-/* Fill CSR columns/values given row_ptr (= nz * prefix sum of the counts). */
+/* Fill CSR columns/values given row_ptr (= nz * prefix sum of the counts).
+ * Value of (row r, cell h, depth k): l_h(r) * K, one rounding, with
+ * K = kdz[t][k] (the same depth kernel under every cell), or, when kdz_cells
+ * is given, K = kdz_cells[h][t][k] (a depth kernel per horizontal cell: the
+ * laterally varying case, where G is no longer l (x) Kdz). */
 int oracle_G_fill(int nx, int ny, int nz, double dx, int64_t n_rows,
                   const double *ctrl, const int32_t *row_period, const double *kdz,
+                  const double *kdz_cells, int n_periods,
                   const int64_t *row_ptr, int32_t *col, double *val)
 {
     int H = nx * ny;
@@ -177,6 +182,8 @@ int oracle_G_fill(int nx, int ny, int nz, double dx, int64_t n_rows,
                 int64_t p = row_ptr[r];
                 for (int i = 0; i < nt; ++i) {
                     int h = touched[i];
+                    if (kdz_cells)
+                        kt = kdz_cells + ((int64_t)h * n_periods + row_period[r]) * nz;
                     for (int k = 0; k < nz; ++k) {
                         col[p] = h * nz + k;
                         val[p] = acc[h] * kt[k];

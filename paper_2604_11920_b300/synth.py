@@ -52,6 +52,7 @@ class Problem:
     seed: int
     m_true: Optional[np.ndarray] = None   # (n,) planted model
     noise: Optional[np.ndarray] = None    # (mG,) unit normal draws
+    kdz_cells: Optional[np.ndarray] = None  # (nx*ny, T, nz): per-cell kernels (lateral case)
 
     @property
     def n(self) -> int:
@@ -121,6 +122,19 @@ def depth_kernel_table(periods_s: np.ndarray, nz: int, dz: float) -> np.ndarray:
     return (z[None, :] / z0) * np.exp(1.0 - z[None, :] / z0) * dz
 
 
+def depth_kernel_cells(periods_s: np.ndarray, nx: int, ny: int, nz: int, dz: float,
+                       amp: float = 0.3) -> np.ndarray:
+    """Laterally varying depth kernels, (nx*ny, T, nz): under cell (ix, iy) the
+    kernel depth is z0 = 1.2 T (1 + amp sin(2 pi (ix+0.5)/nx) cos(2 pi (iy+0.5)/ny)),
+    the stand-in for a 1-D velocity model that changes across the grid; cells
+    ordered h = iy*nx + ix as the columns."""
+    z = (np.arange(nz, dtype=np.float64) + 0.5) * dz
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    f = (np.sin(2.0 * np.pi * (ix + 0.5) / nx) * np.cos(2.0 * np.pi * (iy + 0.5) / ny)).reshape(-1)
+    z0 = 1.2 * np.asarray(periods_s, dtype=np.float64)[None, :, None] * (1.0 + amp * f)[:, None, None]
+    return (z[None, None, :] / z0) * np.exp(1.0 - z[None, None, :] / z0) * dz
+
+
 # ---------------------------------------------------------------- models
 
 def checkerboard(nx: int, ny: int, nz: int, block: int, amp: float) -> np.ndarray:
@@ -162,7 +176,7 @@ def make_problem(name: str, nx: int, ny: int, nz: int, n_stations: int,
                  w: float, lam: float, tol: float, itmax: int, seed: int,
                  dx_km: float = 1.0, dz_km: float = 2.0,
                  checker_block: int = 4, checker_amp: float = 0.05,
-                 blob_amp: float = 0.08) -> Problem:
+                 blob_amp: float = 0.08, lateral: bool = False) -> Problem:
     ss = np.random.SeedSequence(seed)
     r_st, r_ray, r_mod, r_noise = [np.random.default_rng(s) for s in ss.spawn(4)]
     periods = np.asarray(periods_s, dtype=np.float64)
@@ -179,11 +193,12 @@ def make_problem(name: str, nx: int, ny: int, nz: int, n_stations: int,
     else:
         raise ValueError(f"unknown model kind {model!r}")
     noise = r_noise.standard_normal(ctrl.shape[0])
+    kdz_cells = depth_kernel_cells(periods, nx, ny, nz, dz_km) if lateral else None
     return Problem(name=name, nx=nx, ny=ny, nz=nz, dx_km=dx_km, dz_km=dz_km,
                    stations=st, pairs=pairs, periods_s=periods, ctrl=ctrl,
                    row_period=row_period, kdz=kdz, w=w, lam=lam, tol=tol,
                    itmax=itmax, model_kind=model, noise_frac=noise_frac,
-                   seed=seed, m_true=m_true, noise=noise)
+                   seed=seed, m_true=m_true, noise=noise, kdz_cells=kdz_cells)
 
 
 def tiny(seed: int = 0) -> Problem:
@@ -192,6 +207,14 @@ def tiny(seed: int = 0) -> Problem:
     return make_problem("tiny_16x16x8", 16, 16, 8, 20, np.arange(2.0, 17.0, 2.0),
                         bend=0.0, model="checkerboard", noise_frac=0.01,
                         w=1.0, lam=0.1, tol=1e-8, itmax=300, seed=seed)
+
+
+def tiny_lateral(seed: int = 0) -> Problem:
+    """The 16x16x8 system with bent rays and depth kernels that vary across the
+    grid (depth_kernel_cells): G is no longer separable into l (x) Kdz."""
+    return make_problem("tiny_lateral_16x16x8", 16, 16, 8, 20, np.arange(2.0, 17.0, 2.0),
+                        bend=0.15, model="checkerboard", noise_frac=0.01,
+                        w=1.0, lam=0.1, tol=1e-8, itmax=300, seed=seed, lateral=True)
 
 
 def mid(seed: int = 1) -> Problem:

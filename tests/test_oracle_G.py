@@ -147,3 +147,46 @@ def test_spmv_matches_scipy(tiny_system):
     _, G, _, _ = tiny_system
     x = np.random.default_rng(3).standard_normal(G.n_cols)
     np.testing.assert_allclose(oracle.spmv(G, x), G.to_scipy() @ x, rtol=1e-13, atol=1e-12)
+
+
+# ------------------------------------------------ laterally varying kernels
+
+def test_lateral_values_are_length_times_cell_kernel():
+    """With a depth kernel per horizontal cell, every value is the ray length
+    in the cell times that cell's kernel: l_h comes from the same rays built
+    with an all-ones kernel table (value = l_h * 1 exactly), then one
+    multiplication by kdz_cells[h][t][k]."""
+    from paper_2604_11920_b300 import synth
+    p = synth.tiny_lateral()
+    G = oracle.build_G_problem(p)
+    ones = oracle.build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period,
+                          np.ones_like(p.kdz))
+    assert np.array_equal(G.ptr, ones.ptr) and np.array_equal(G.idx, ones.idx)
+    rows = np.repeat(np.arange(G.n_rows), np.diff(G.ptr))
+    h, k = G.idx // p.nz, G.idx % p.nz
+    want = ones.val * p.kdz_cells[h, p.row_period[rows], k]
+    assert np.array_equal(G.val, want)
+    # the separable table under the same rays gives other values
+    sep = oracle.build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, p.kdz)
+    assert not np.allclose(G.val, sep.val)
+
+
+def test_lateral_kernels_break_separability():
+    """Two cells of one row: the ratio of their depth profiles varies with
+    depth when their kernels differ (it is constant in the separable case)."""
+    from paper_2604_11920_b300 import synth
+    p = synth.tiny_lateral()
+    G = oracle.build_G_problem(p)
+    nz = p.nz
+    found = False
+    for r in range(G.n_rows):
+        a, b = G.ptr[r], G.ptr[r + 1]
+        if b - a < 2 * nz:
+            continue
+        c0 = G.val[a:a + nz]
+        c1 = G.val[a + nz:a + 2 * nz]
+        ratio = c0 / c1
+        if np.ptp(ratio) > 1e-3 * np.abs(ratio).max():
+            found = True
+            break
+    assert found
