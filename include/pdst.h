@@ -77,6 +77,11 @@ typedef struct {
 typedef struct {
     uint32_t value_dtypes; /* bit mask of (1u << pdst_dtype) value copies to keep; 0 = F64|F32 */
     uint32_t formats;      /* bit mask of (1u << pdst_format) index layouts; 0 = both */
+    const double *kdz_cells; /* optional host table (nx*ny x n_periods x nz, cell h = iy*nx+ix
+                                slowest, depth fastest): a depth kernel per horizontal cell,
+                                value (r, h, k) = l_h(r) * kdz_cells[h][t(r)][k] (laterally
+                                varying 1-D models under Eq. 5); NULL: kdz for every cell.
+                                Copied; must be finite. */
 } pdst_build_opts;
 
 /*

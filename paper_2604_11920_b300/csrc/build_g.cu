@@ -182,19 +182,26 @@ __global__ void k_fill_cells(int64_t m, const double *__restrict__ ctrl, int nx,
     }
 }
 
-// vals[nz*e + k] = l_e * Kdz[t(row(e))][k] in FP64, plus narrower copies.
+// vals[nz*e + k] = l_e * K in FP64, plus narrower copies, with K = Kdz[t][k]
+// (t the period of run e's row) or, given a per-cell table, Kc[h][t][k] (h
+// the run's cell).
 __global__ void k_expand_values(int64_t U, int nz, const double *__restrict__ lens,
                                 const int32_t *__restrict__ run_row,
                                 const int32_t *__restrict__ row_period,
-                                const double *__restrict__ kdz, double *v64, float *v32,
-                                __nv_bfloat16 *vbf) {
+                                const double *__restrict__ kdz,
+                                const int32_t *__restrict__ run_cell,
+                                const double *__restrict__ kdz_cells, int n_periods,
+                                double *v64, float *v32, __nv_bfloat16 *vbf) {
     int64_t total = U * nz;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t e = i / nz;
         int k = (int)(i - e * nz);
         int t = row_period[run_row[e]];
-        double v = __dmul_rn(lens[e], kdz[(int64_t)t * nz + k]);
+        const double kv = kdz_cells
+                              ? kdz_cells[((int64_t)run_cell[e] * n_periods + t) * nz + k]
+                              : kdz[(int64_t)t * nz + k];
+        double v = __dmul_rn(lens[e], kv);
         if (v64) v64[i] = v;
         if (v32) v32[i] = __double2float_rn(v);
         if (vbf) vbf[i] = __double2bfloat16(v);
@@ -442,7 +449,8 @@ static unsigned grid_for(int64_t work, int threads, int device) {
 }
 
 static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int32_t *per_host,
-                              const double *kdz_host, uint32_t dtypes, cudaStream_t s) {
+                              const double *kdz_host, const double *kdz_cells_host,
+                              uint32_t dtypes, cudaStream_t s) {
     const int nx = h->grid.nx, ny = h->grid.ny, nz = h->nz, H = h->H;
     const double dx = h->grid.dx_km;
     const int64_t m = h->m;
@@ -470,6 +478,12 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
     DevBuf d_ctrl, d_kdz, d_cnt, d_err, d_lens, d_runrow, d_runpos;
     PDST_TRY(d_ctrl.alloc(sizeof(double) * 6 * std::max<int64_t>(m, 1)));
     PDST_TRY(d_kdz.alloc(sizeof(double) * (size_t)h->n_periods * nz));
+    DevBuf d_kcells;
+    if (kdz_cells_host) {
+        const size_t kb = sizeof(double) * (size_t)H * h->n_periods * nz;
+        PDST_TRY(d_kcells.alloc(kb));
+        PDST_CUDA(cudaMemcpyAsync(d_kcells.p, kdz_cells_host, kb, cudaMemcpyHostToDevice, s));
+    }
     PDST_TRY(h->row_period.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1)));
     PDST_TRY(d_cnt.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1)));
     PDST_TRY(d_err.alloc(sizeof(int)));
@@ -538,7 +552,8 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
     if (nnz) {
         k_expand_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
             U, nz, d_lens.as<double>(), d_runrow.as<int32_t>(), h->row_period.as<int32_t>(),
-            d_kdz.as<double>(), v64,
+            d_kdz.as<double>(), h->row_cells.as<int32_t>(),
+            kdz_cells_host ? d_kcells.as<double>() : nullptr, h->n_periods, v64,
             h->vals[1].present ? h->vals[1].csr.as<float>() : nullptr,
             h->vals[2].present ? h->vals[2].csr.as<__nv_bfloat16>() : nullptr);
         PDST_CUDA(cudaGetLastError());
@@ -705,6 +720,10 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
                        "pdst_build_G: period index of path %lld out of range", (long long)r);
     for (int64_t i = 0; i < (int64_t)n_periods * grid->nz; ++i)
         PDST_CHECK_ARG(std::isfinite(kdz_host[i]), "pdst_build_G: non-finite kdz entry");
+    const double *kdz_cells = opts ? opts->kdz_cells : nullptr;
+    if (kdz_cells)
+        for (int64_t i = 0; i < H * n_periods * grid->nz; ++i)
+            PDST_CHECK_ARG(std::isfinite(kdz_cells[i]), "pdst_build_G: non-finite kdz_cells entry");
     uint32_t dtypes = opts && opts->value_dtypes ? opts->value_dtypes
                                                  : (1u << PDST_F64) | (1u << PDST_F32);
     uint32_t formats = opts && opts->formats ? opts->formats
@@ -723,7 +742,7 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
     h->nz = grid->nz;
     h->n_periods = n_periods;
     h->formats = formats;
-    pdst_status st = build_impl(h, ctrl_host, path_period_host, kdz_host, dtypes,
+    pdst_status st = build_impl(h, ctrl_host, path_period_host, kdz_host, kdz_cells, dtypes,
                                 (cudaStream_t)stream);
     if (st != PDST_OK) {
         delete h;
