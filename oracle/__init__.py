@@ -52,11 +52,11 @@ def _load():
         build()
         lib = ctypes.CDLL(_LIB)
         lib.oracle_G_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_int64, _d, _i32]
+                                       ctypes.c_int, ctypes.c_int64, _d, _i32]
         lib.oracle_G_count.restype = ctypes.c_int
         lib.oracle_G_fill.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_int64, _d, _i32, _d, _d, ctypes.c_int, _i64,
-                                      _i32, _d]
+                                      ctypes.c_int, ctypes.c_int64, _d, _i32, _d, _d,
+                                      ctypes.c_int, _i64, _i32, _d]
         lib.oracle_G_fill.restype = ctypes.c_int
         lib.oracle_transpose.argtypes = [ctypes.c_int64, ctypes.c_int32, _i64, _i32, _d,
                                          _i64, _i32, _d]
@@ -119,9 +119,12 @@ class CSR:
 
 
 def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
-            row_period: np.ndarray, kdz: np.ndarray, kdz_cells=None) -> CSR:
+            row_period: np.ndarray, kdz: np.ndarray, kdz_cells=None, interp: int = 0) -> CSR:
     """Sensitivity matrix G (rows = paths in the order given) as CSR; with
-    kdz_cells (nx*ny, periods, nz) a depth kernel per horizontal cell."""
+    kdz_cells (nx*ny, periods, nz) a depth kernel per horizontal cell; interp 1:
+    bilinear node coefficients instead of cell lengths."""
+    if interp not in (0, 1) or (interp == 1 and (nx < 2 or ny < 2)):
+        raise ValueError("interp must be 0, or 1 on a grid of at least 2 x 2 nodes")
     lib = _load()
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 6)
     row_period = np.ascontiguousarray(row_period, dtype=np.int32)
@@ -132,7 +135,7 @@ def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
     if m and (row_period.min() < 0 or row_period.max() >= kdz.shape[0]):
         raise ValueError("period index out of range")
     cells = np.zeros(m, dtype=np.int32)
-    if lib.oracle_G_count(nx, ny, dx_km, m, _p(ctrl, _d), _p(cells, _i32)) != 0:
+    if lib.oracle_G_count(nx, ny, dx_km, interp, m, _p(ctrl, _d), _p(cells, _i32)) != 0:
         raise MemoryError("oracle_G_count")
     ptr = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(cells.astype(np.int64) * nz, out=ptr[1:])
@@ -144,7 +147,8 @@ def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
         kc = np.ascontiguousarray(kdz_cells, dtype=np.float64)
         if kc.shape != (nx * ny, kdz.shape[0], nz):
             raise ValueError("kdz_cells must be (nx*ny, periods, nz)")
-    if lib.oracle_G_fill(nx, ny, nz, dx_km, m, _p(ctrl, _d), _p(row_period, _i32), _p(kdz, _d),
+    if lib.oracle_G_fill(nx, ny, nz, dx_km, interp, m, _p(ctrl, _d), _p(row_period, _i32),
+                         _p(kdz, _d),
                          _p(kc, _d), int(kdz.shape[0]), _p(ptr, _i64), _p(col, _i32),
                          _p(val, _d)) != 0:
         raise MemoryError("oracle_G_fill")
@@ -153,7 +157,7 @@ def build_G(nx: int, ny: int, nz: int, dx_km: float, ctrl: np.ndarray,
 
 def build_G_problem(p) -> CSR:
     return build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, p.kdz,
-                   getattr(p, "kdz_cells", None))
+                   getattr(p, "kdz_cells", None), getattr(p, "interp", 0))
 
 
 def transpose(G: CSR) -> CSR:

@@ -92,7 +92,42 @@ static int cmp_int(const void *a, const void *b)
 
 /* Walk one ray: acc[h] += chord length for every chord, in chord order.
  * touched[] receives each newly hit cell once; returns how many. */
-static int walk_ray(const double *c, int nx, int ny, double dx, double *acc,
+/* Lower node of the bilinear interpolation along one axis and the fraction
+ * towards the next node: nodes at (i + 1/2) dx, i = 0..n-1 (cell centres);
+ * i0 = floor(coord/dx - 1/2) clamped to [0, n-2], t = coord/dx - 1/2 - i0
+ * clamped to [0, 1]. */
+static int bilin_axis(double coord, double dx, int n, double *t)
+{
+    double f = coord / dx - 0.5;
+    double i0 = floor(f);
+    if (i0 < 0.0)
+        i0 = 0.0;
+    if (i0 > (double)(n - 2))
+        i0 = (double)(n - 2);
+    double tt = f - i0;
+    if (tt < 0.0)
+        tt = 0.0;
+    if (tt > 1.0)
+        tt = 1.0;
+    *t = tt;
+    return (int)i0;
+}
+
+static void add_to(int h, double v, double *acc, unsigned char *seen, int *touched, int *nt)
+{
+    if (!seen[h]) {
+        seen[h] = 1;
+        acc[h] = 0.0;
+        touched[(*nt)++] = h;
+    }
+    acc[h] = acc[h] + v;
+}
+
+/* Walk one ray: interp 0 gives each chord's length to the cell holding its
+ * midpoint; interp 1 (Eq. 1's bilinear coefficients v_ik) splits it over the
+ * four grid nodes around the midpoint with bilinear weights, in the order
+ * (i0, j0), (i0+1, j0), (i0, j0+1), (i0+1, j0+1). */
+static int walk_ray(const double *c, int nx, int ny, double dx, int interp, double *acc,
                     unsigned char *seen, int *touched)
 {
     int64_t N = chord_count(c, dx);
@@ -108,15 +143,20 @@ static int walk_ray(const double *c, int nx, int ny, double dx, double *acc,
         double ex = qx - px, ey = qy - py;
         double len = sqrt(ex * ex + ey * ey);
         double mx = 0.5 * (px + qx), my = 0.5 * (py + qy);
-        int ix = clamp_cell(mx, dx, nx);
-        int iy = clamp_cell(my, dx, ny);
-        int h = iy * nx + ix;
-        if (!seen[h]) {
-            seen[h] = 1;
-            acc[h] = 0.0;
-            touched[nt++] = h;
+        if (interp == 0) {
+            int ix = clamp_cell(mx, dx, nx);
+            int iy = clamp_cell(my, dx, ny);
+            add_to(iy * nx + ix, len, acc, seen, touched, &nt);
+        } else {
+            double tx, ty;
+            int ix = bilin_axis(mx, dx, nx, &tx);
+            int iy = bilin_axis(my, dx, ny, &ty);
+            double a = 1.0 - tx, b = 1.0 - ty;
+            add_to(iy * nx + ix, len * (a * b), acc, seen, touched, &nt);
+            add_to(iy * nx + ix + 1, len * (tx * b), acc, seen, touched, &nt);
+            add_to((iy + 1) * nx + ix, len * (a * ty), acc, seen, touched, &nt);
+            add_to((iy + 1) * nx + ix + 1, len * (tx * ty), acc, seen, touched, &nt);
         }
-        acc[h] = acc[h] + len;
         px = qx;
         py = qy;
     }
@@ -124,7 +164,7 @@ static int walk_ray(const double *c, int nx, int ny, double dx, double *acc,
 }
 
 /* Per-row number of distinct cells hit (row r has cells[r] * nz entries). */
-int oracle_G_count(int nx, int ny, double dx, int64_t n_rows, const double *ctrl,
+int oracle_G_count(int nx, int ny, double dx, int interp, int64_t n_rows, const double *ctrl,
                    int32_t *cells_out)
 {
     int H = nx * ny;
@@ -140,7 +180,7 @@ int oracle_G_count(int nx, int ny, double dx, int64_t n_rows, const double *ctrl
         } else {
 #pragma omp for schedule(dynamic, 64)
             for (int64_t r = 0; r < n_rows; ++r) {
-                int nt = walk_ray(ctrl + 6 * r, nx, ny, dx, acc, seen, touched);
+                int nt = walk_ray(ctrl + 6 * r, nx, ny, dx, interp, acc, seen, touched);
                 cells_out[r] = nt;
                 for (int i = 0; i < nt; ++i)
                     seen[touched[i]] = 0;
@@ -158,7 +198,7 @@ int oracle_G_count(int nx, int ny, double dx, int64_t n_rows, const double *ctrl
  * K = kdz[t][k] (the same depth kernel under every cell), or, when kdz_cells
  * is given, K = kdz_cells[h][t][k] (a depth kernel per horizontal cell: the
  * laterally varying case, where G is no longer l (x) Kdz). */
-int oracle_G_fill(int nx, int ny, int nz, double dx, int64_t n_rows,
+int oracle_G_fill(int nx, int ny, int nz, double dx, int interp, int64_t n_rows,
                   const double *ctrl, const int32_t *row_period, const double *kdz,
                   const double *kdz_cells, int n_periods,
                   const int64_t *row_ptr, int32_t *col, double *val)
@@ -176,7 +216,7 @@ int oracle_G_fill(int nx, int ny, int nz, double dx, int64_t n_rows,
         } else {
 #pragma omp for schedule(dynamic, 64)
             for (int64_t r = 0; r < n_rows; ++r) {
-                int nt = walk_ray(ctrl + 6 * r, nx, ny, dx, acc, seen, touched);
+                int nt = walk_ray(ctrl + 6 * r, nx, ny, dx, interp, acc, seen, touched);
                 qsort(touched, (size_t)nt, sizeof(int), cmp_int);
                 const double *kt = kdz + (int64_t)row_period[r] * nz;
                 int64_t p = row_ptr[r];

@@ -53,6 +53,7 @@ class Problem:
     m_true: Optional[np.ndarray] = None   # (n,) planted model
     noise: Optional[np.ndarray] = None    # (mG,) unit normal draws
     kdz_cells: Optional[np.ndarray] = None  # (nx*ny, T, nz): per-cell kernels (lateral case)
+    interp: int = 0                       # 0: cell lengths; 1: bilinear node coefficients (Eq. 1)
 
     @property
     def n(self) -> int:
@@ -176,7 +177,7 @@ def make_problem(name: str, nx: int, ny: int, nz: int, n_stations: int,
                  w: float, lam: float, tol: float, itmax: int, seed: int,
                  dx_km: float = 1.0, dz_km: float = 2.0,
                  checker_block: int = 4, checker_amp: float = 0.05,
-                 blob_amp: float = 0.08, lateral: bool = False) -> Problem:
+                 blob_amp: float = 0.08, lateral: bool = False, interp: int = 0) -> Problem:
     ss = np.random.SeedSequence(seed)
     r_st, r_ray, r_mod, r_noise = [np.random.default_rng(s) for s in ss.spawn(4)]
     periods = np.asarray(periods_s, dtype=np.float64)
@@ -198,7 +199,7 @@ def make_problem(name: str, nx: int, ny: int, nz: int, n_stations: int,
                    stations=st, pairs=pairs, periods_s=periods, ctrl=ctrl,
                    row_period=row_period, kdz=kdz, w=w, lam=lam, tol=tol,
                    itmax=itmax, model_kind=model, noise_frac=noise_frac,
-                   seed=seed, m_true=m_true, noise=noise, kdz_cells=kdz_cells)
+                   seed=seed, m_true=m_true, noise=noise, kdz_cells=kdz_cells, interp=interp)
 
 
 def tiny(seed: int = 0) -> Problem:
@@ -215,6 +216,15 @@ def tiny_lateral(seed: int = 0) -> Problem:
     return make_problem("tiny_lateral_16x16x8", 16, 16, 8, 20, np.arange(2.0, 17.0, 2.0),
                         bend=0.15, model="checkerboard", noise_frac=0.01,
                         w=1.0, lam=0.1, tol=1e-8, itmax=300, seed=seed, lateral=True)
+
+
+def tiny_bilinear(seed: int = 0) -> Problem:
+    """The 16x16x8 system with bent rays, laterally varying kernels and Eq. 1's
+    bilinear node coefficients (each chord split over the four nodes around it)."""
+    return make_problem("tiny_bilinear_16x16x8", 16, 16, 8, 20, np.arange(2.0, 17.0, 2.0),
+                        bend=0.15, model="checkerboard", noise_frac=0.01,
+                        w=1.0, lam=0.1, tol=1e-8, itmax=300, seed=seed, lateral=True,
+                        interp=1)
 
 
 def mid(seed: int = 1) -> Problem:

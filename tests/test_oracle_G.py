@@ -190,3 +190,37 @@ def test_lateral_kernels_break_separability():
             found = True
             break
     assert found
+
+
+# ------------------------------------------------ bilinear node coefficients
+
+def test_bilinear_straight_ray_along_a_node_row():
+    """Ray along the node row y = 1.5 of an 8 x 4 grid (dx = 1), x from 0 to 8:
+    32 chords of 0.25 whose boundaries fall on the nodes, so the midpoint rule
+    integrates each node's hat function exactly: every node of the row gets
+    length 1 (the edge nodes take the clamped ends), the next row's nodes are
+    touched with weight 0."""
+    ctrl = np.array([[0.0, 1.5, 4.0, 1.5, 8.0, 1.5]])
+    G = oracle.build_G(8, 4, 1, 1.0, ctrl, np.zeros(1, np.int32), np.ones((1, 1)), interp=1)
+    vals = dict(zip(G.idx.tolist(), G.val.tolist()))
+    for ix in range(8):
+        assert abs(vals[1 * 8 + ix] - 1.0) <= 1e-14
+        assert vals[2 * 8 + ix] == 0.0
+    assert set(vals) == {1 * 8 + ix for ix in range(8)} | {2 * 8 + ix for ix in range(8)}
+
+
+def test_bilinear_coefficients_partition_the_path():
+    """The four weights of a chord sum to one, so each row's coefficients sum
+    to the same total length as the cell form."""
+    from paper_2604_11920_b300 import synth
+    p = synth.tiny_bilinear()
+    ones = np.ones_like(p.kdz)
+    Gb = oracle.build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, ones, interp=1)
+    Gc = oracle.build_G(p.nx, p.ny, p.nz, p.dx_km, p.ctrl, p.row_period, ones, interp=0)
+    rb = np.add.reduceat(Gb.val, Gb.ptr[:-1]) / p.nz
+    rc = np.add.reduceat(Gc.val, Gc.ptr[:-1]) / p.nz
+    np.testing.assert_allclose(rb, rc, rtol=1e-12)
+    # a band of nodes: more columns per row than the cell form
+    assert Gb.nnz > 1.5 * Gc.nnz
+    with pytest.raises(ValueError):
+        oracle.build_G(1, 4, 1, 1.0, p.ctrl[:1], p.row_period[:1], ones, interp=1)
