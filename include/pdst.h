@@ -82,6 +82,12 @@ typedef struct {
                                 value (r, h, k) = l_h(r) * kdz_cells[h][t(r)][k] (laterally
                                 varying 1-D models under Eq. 5); NULL: kdz for every cell.
                                 Copied; must be finite. */
+    int32_t interp;        /* 0 (default): each chord's length goes to the cell holding its
+                              midpoint; 1: Eq. 1's bilinear interpolation coefficients v_ik,
+                              each chord's length split over the four grid nodes around its
+                              midpoint (nodes at cell centres, so the columns keep the cell
+                              numbering; needs nx, ny >= 2) */
+    int32_t reserved0;
 } pdst_build_opts;
 
 /*

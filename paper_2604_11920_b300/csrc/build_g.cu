@@ -61,13 +61,31 @@ __device__ __forceinline__ int cell_of(double coord, double dx, int ncell) {
     return (int)f;
 }
 
+// Lower node and fraction of the bilinear interpolation along one axis:
+// nodes at (i + 1/2) dx; i0 = floor(coord/dx - 1/2) clamped to [0, n-2],
+// t = coord/dx - 1/2 - i0 clamped to [0, 1].
+__device__ __forceinline__ int bilin_axis(double coord, double dx, int n, double &t) {
+    const double f = __dsub_rn(__ddiv_rn(coord, dx), 0.5);
+    double i0 = floor(f);
+    if (i0 < 0.0) i0 = 0.0;
+    if (i0 > (double)(n - 2)) i0 = (double)(n - 2);
+    double tt = __dsub_rn(f, i0);
+    if (tt < 0.0) tt = 0.0;
+    if (tt > 1.0) tt = 1.0;
+    t = tt;
+    return (int)i0;
+}
+
 // One warp walks one ray.  The 32 lanes evaluate 32 consecutive chords at a
 // time; the per-cell sums are then advanced in chord order (every lane holds
-// the same running sum, so the result does not depend on the lane).  The
-// distinct cells live in a per-warp shared-memory list of capacity `cap`.
-// Returns the number of distinct cells (> cap means the list overflowed).
-__device__ int walk_ray_warp(const Ray &c, int nx, int ny, double dx, int cap, int *lc,
-                             double *la) {
+// the same running sum, so the result does not depend on the lane).  With
+// interp 1 a chord gives len * w to the four nodes around its midpoint
+// (bilinear weights w, Eq. 1's coefficients), in the order (i0, j0),
+// (i0+1, j0), (i0, j0+1), (i0+1, j0+1).  The distinct cells (nodes) live in a
+// per-warp shared-memory list of capacity `cap`.  Returns the number of
+// distinct cells (> cap means the list overflowed).
+__device__ int walk_ray_warp(const Ray &c, int nx, int ny, double dx, int interp, int cap,
+                             int *lc, double *la) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int64_t N = chord_count_dev(c, dx);
@@ -85,20 +103,39 @@ __device__ int walk_ray_warp(const Ray &c, int nx, int ny, double dx, int cap, i
             px = cx;
             py = cy;
         }
-        double len = 0.0;
-        int cell = 0;
+        const int np = interp ? 4 : 1;   // contributions per chord
+        double len[4] = {0.0, 0.0, 0.0, 0.0};
+        int cell[4] = {0, 0, 0, 0};
         if (valid) {
-            len = hyp(__dsub_rn(qx, px), __dsub_rn(qy, py));
+            const double l = hyp(__dsub_rn(qx, px), __dsub_rn(qy, py));
             double mx = __dmul_rn(0.5, __dadd_rn(px, qx));
             double my = __dmul_rn(0.5, __dadd_rn(py, qy));
-            cell = cell_of(my, dx, ny) * nx + cell_of(mx, dx, nx);
+            if (!interp) {
+                len[0] = l;
+                cell[0] = cell_of(my, dx, ny) * nx + cell_of(mx, dx, nx);
+            } else {
+                double tx, ty;
+                const int ix = bilin_axis(mx, dx, nx, tx), iy = bilin_axis(my, dx, ny, ty);
+                const double a = __dsub_rn(1.0, tx), b = __dsub_rn(1.0, ty);
+                cell[0] = iy * nx + ix;
+                cell[1] = iy * nx + ix + 1;
+                cell[2] = (iy + 1) * nx + ix;
+                cell[3] = (iy + 1) * nx + ix + 1;
+                len[0] = __dmul_rn(l, __dmul_rn(a, b));
+                len[1] = __dmul_rn(l, __dmul_rn(tx, b));
+                len[2] = __dmul_rn(l, __dmul_rn(a, ty));
+                len[3] = __dmul_rn(l, __dmul_rn(tx, ty));
+            }
         }
         cx = __shfl_sync(full, qx, 31);
         cy = __shfl_sync(full, qy, 31);
         int nvalid = (int)((N - base) < 32 ? (N - base) : 32);
-        for (int j = 0; j < nvalid; ++j) {
-            int cj = __shfl_sync(full, cell, j);
-            double lj = __shfl_sync(full, len, j);
+        for (int jj = 0; jj < nvalid * np; ++jj) {
+            const int j = jj / np, q = jj - j * np;
+            const int mine = q == 0 ? cell[0] : q == 1 ? cell[1] : q == 2 ? cell[2] : cell[3];
+            const double lmine = q == 0 ? len[0] : q == 1 ? len[1] : q == 2 ? len[2] : len[3];
+            int cj = __shfl_sync(full, mine, j);
+            double lj = __shfl_sync(full, lmine, j);
             if (cj != cur_cell) {
                 if (lane == 0 && cur_slot >= 0 && cur_slot < cap) la[cur_slot] = cur;
                 __syncwarp();
@@ -139,13 +176,14 @@ __device__ __forceinline__ Ray load_ray(const double *ctrl, int64_t r) {
 
 // Pass 1: distinct cells per row.
 __global__ void k_count_cells(int64_t m, const double *__restrict__ ctrl, int nx, int ny,
-                              double dx, int cap, int32_t *__restrict__ cnt, int *err) {
+                              double dx, int interp, int cap, int32_t *__restrict__ cnt,
+                              int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
     double *la = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
     int *lc = reinterpret_cast<int *>(smem + (size_t)wpb * cap * sizeof(double)) + (size_t)warp * cap;
     for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < m; r += (int64_t)gridDim.x * wpb) {
-        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, cap, lc, la);
+        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, interp, cap, lc, la);
         if ((threadIdx.x & 31) == 0) {
             cnt[r] = u;
             if (u > cap) atomicExch(err, 1);
@@ -156,7 +194,7 @@ __global__ void k_count_cells(int64_t m, const double *__restrict__ ctrl, int nx
 // Pass 2: walk again, sort the row's cells ascending (rank of unique keys)
 // and write cells, per-cell lengths and the owning row of every run.
 __global__ void k_fill_cells(int64_t m, const double *__restrict__ ctrl, int nx, int ny,
-                             double dx, int cap, const int64_t *__restrict__ cptr,
+                             double dx, int interp, int cap, const int64_t *__restrict__ cptr,
                              int32_t *__restrict__ cells, double *__restrict__ lens,
                              int32_t *__restrict__ run_row, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -164,7 +202,7 @@ __global__ void k_fill_cells(int64_t m, const double *__restrict__ ctrl, int nx,
     double *la = reinterpret_cast<double *>(smem) + (size_t)warp * cap;
     int *lc = reinterpret_cast<int *>(smem + (size_t)wpb * cap * sizeof(double)) + (size_t)warp * cap;
     for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < m; r += (int64_t)gridDim.x * wpb) {
-        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, cap, lc, la);
+        int u = walk_ray_warp(load_ray(ctrl, r), nx, ny, dx, interp, cap, lc, la);
         int64_t base = cptr[r];
         if (u > cap || (int64_t)u != cptr[r + 1] - base) {
             if (lane == 0) atomicExch(err, 2);
@@ -458,7 +496,9 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
     // capacity of the per-warp distinct-cell list (distinct cells <= chords)
     int64_t maxN = 0;
     for (int64_t r = 0; r < m; ++r) maxN = std::max(maxN, host_chord_count(ctrl_host + 6 * r, dx));
-    int64_t cap64 = std::min<int64_t>(maxN + 64, H);
+    // distinct cells a ray can touch: one per chord (four nodes per chord
+    // with bilinear coefficients)
+    int64_t cap64 = std::min<int64_t>((h->interp ? 4 : 1) * maxN + 64, H);
     cap64 = (cap64 + 31) / 32 * 32;
     if (cap64 < 32) cap64 = 32;
     const int64_t smem_budget = 200 * 1024;
@@ -501,7 +541,8 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
     unsigned wgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + wpb - 1) / wpb,
                                                                       (int64_t)sms * 8));
     if (m) {
-        k_count_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx, cap,
+        k_count_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx,
+                                                   h->interp, cap,
                                                    d_cnt.as<int32_t>(), d_err.as<int>());
         PDST_CUDA(cudaGetLastError());
     }
@@ -524,7 +565,8 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
     PDST_TRY(d_lens.alloc(sizeof(double) * std::max<int64_t>(U, 1)));
     PDST_TRY(d_runrow.alloc(sizeof(int32_t) * std::max<int64_t>(U, 1)));
     if (m) {
-        k_fill_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx, cap,
+        k_fill_cells<<<wgrid, wpb * 32, smem, s>>>(m, d_ctrl.as<double>(), nx, ny, dx,
+                                                  h->interp, cap,
                                                   h->row_cptr.as<int64_t>(),
                                                   h->row_cells.as<int32_t>(), d_lens.as<double>(),
                                                   d_runrow.as<int32_t>(), d_err.as<int>());
@@ -730,6 +772,9 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
                                              : (1u << PDST_FMT_ELEMENT) | (1u << PDST_FMT_BLOCKED);
     PDST_CHECK_ARG((dtypes & ~15u) == 0, "pdst_build_G: unknown value dtype bits");
     PDST_CHECK_ARG((formats & ~3u) == 0, "pdst_build_G: unknown format bits");
+    const int interp = opts ? opts->interp : 0;
+    PDST_CHECK_ARG(interp == 0 || (interp == 1 && grid->nx >= 2 && grid->ny >= 2),
+                   "pdst_build_G: interp must be 0, or 1 on a grid of at least 2 x 2 nodes");
 
     static std::atomic<uint64_t> next_uid{1};
     pdst_handle *h = new pdst_handle();
@@ -742,6 +787,7 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
     h->nz = grid->nz;
     h->n_periods = n_periods;
     h->formats = formats;
+    h->interp = interp;
     pdst_status st = build_impl(h, ctrl_host, path_period_host, kdz_host, kdz_cells, dtypes,
                                 (cudaStream_t)stream);
     if (st != PDST_OK) {

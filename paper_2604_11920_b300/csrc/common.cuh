@@ -168,6 +168,7 @@ struct pdst_handle {
     pdst::DevBuf cell_order;   // int32 [H]    cells by descending row count (work order)
     pdst::DevBuf adj_item;     // int32 [2*n_adj]  (cell, first row) of each adjoint work item
     int32_t adj_chunk = 256;   // rows of one cell per adjoint work item
+    int32_t interp = 0;        // 0 cell lengths, 1 bilinear node coefficients
     int64_t n_adj = 0;         // adjoint work items: chunks of ADJ_CHUNK rows, longest cells first
     // element indices (PDST_FMT_ELEMENT)
     pdst::DevBuf row_ptr;      // int64 [m+1]

@@ -42,7 +42,8 @@ class Grid(ctypes.Structure):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("value_dtypes", ctypes.c_uint32), ("formats", ctypes.c_uint32),
-                ("kdz_cells", ctypes.c_void_p)]
+                ("kdz_cells", ctypes.c_void_p), ("interp", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class LsqrOpts(ctypes.Structure):
@@ -316,7 +317,7 @@ class Handle:
 
 
 def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=("f64", "f32"),
-            formats=("element", "blocked"), stream=None, kdz_cells=None) -> Handle:
+            formats=("element", "blocked"), stream=None, kdz_cells=None, interp=0) -> Handle:
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 6)
     row_period = np.ascontiguousarray(row_period, dtype=np.int32)
     kdz = np.ascontiguousarray(kdz, dtype=np.float64)
@@ -327,7 +328,7 @@ def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=(
         if kc.shape != (nx * ny, int(n_periods), nz):
             raise ValueError("kdz_cells must be (nx*ny, n_periods, nz)")
     opts = BuildOpts(sum(1 << DTYPES[d] for d in dtypes), sum(1 << FORMATS[f] for f in formats),
-                     None if kc is None else kc.ctypes.data)
+                     None if kc is None else kc.ctypes.data, int(interp), 0)
     out = ctypes.c_void_p()
     _check(load().pdst_build_G(ctypes.byref(grid), ctrl.shape[0], _np_ptr(ctrl),
                                _np_ptr(row_period), int(n_periods), _np_ptr(kdz),
@@ -338,6 +339,7 @@ def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=(
 def build_G_problem(p, **kw) -> Handle:
     """pdst_build_G for a generator problem (see synth.py)."""
     kw.setdefault("kdz_cells", getattr(p, "kdz_cells", None))
+    kw.setdefault("interp", getattr(p, "interp", 0))
     return build_G(p.nx, p.ny, p.nz, p.dx_km, p.dz_km, p.ctrl, p.row_period, p.n_periods,
                    p.kdz, **kw)
 

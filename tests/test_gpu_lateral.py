@@ -61,3 +61,47 @@ def test_lateral_bad_table_rejected(lateral):
         pdst.build_G_problem(p, dtypes=("f64",), kdz_cells=bad)
     with pytest.raises(ValueError):
         pdst.build_G_problem(p, dtypes=("f64",), kdz_cells=bad[:-1])
+
+
+# ------------------------------------------------ bilinear node coefficients (Eq. 1)
+
+@pytest.fixture(scope="module")
+def bilinear():
+    require_cuda()
+    p = synth.tiny_bilinear()
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    h = pdst.build_G_problem(p, dtypes=("f64", "f32"))
+    return p, G, GT, d, h
+
+
+def test_bilinear_G_bit_exact(bilinear):
+    p, G, GT, d, h = bilinear
+    ptr, idx, val = h.export_csr("f64")
+    assert np.array_equal(ptr, G.ptr) and np.array_equal(idx, G.idx)
+    assert np.array_equal(val, G.val)
+    cptr, cidx, cval = h.export_csc("f64")
+    assert np.array_equal(cptr, GT.ptr) and np.array_equal(cidx, GT.idx)
+    assert np.array_equal(cval, GT.val)
+    hc = pdst.build_G_problem(p, dtypes=("f64",), interp=0)
+    assert hc.nnz < G.nnz          # the cell form touches fewer columns per row
+    hc.close()
+
+
+def test_bilinear_lsqr_matches_oracle(bilinear):
+    p, G, GT, d, h = bilinear
+    ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=1e-12, btol=1e-12,
+                      itmax=50000)
+    res = h.lsqr(to_dev(d), p.w, p.lam, 50000, 1e-10, fmt="blocked")
+    assert res.info["istop"] in (1, 2)
+    assert rel(res.m.cpu().numpy(), ref.x) <= 1e-4
+    r32 = h.lsqr(to_dev(d), p.w, p.lam, 50000, 1e-6, dtype="f32", fmt="blocked")
+    assert r32.info["istop"] in (1, 2)
+
+
+def test_bilinear_needs_two_nodes_per_axis(bilinear):
+    p, G, GT, d, h = bilinear
+    with pytest.raises(pdst.PdstError):
+        pdst.build_G(1, 4, 2, 1.0, 2.0, p.ctrl[:3], p.row_period[:3], p.n_periods, p.kdz,
+                     dtypes=("f64",), interp=1)
