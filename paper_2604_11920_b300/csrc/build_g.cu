@@ -313,10 +313,11 @@ __global__ void k_bcsc_values(int64_t U, int nz, const int64_t *__restrict__ run
 // streaming a few hundred rows, so items are made as long as the load balance
 // allows: the largest power of two in [ADJ_CHUNK_MIN, ADJ_CHUNK_MAX] that still
 // gives at least ITEMS_PER_WARP items to each resident warp of the adjoint
-// sweep (32 per SM).  Measured on B300 (FP32 sweep): 512 rows best on the
-// 64 x 64 x 16 system, 2048 on the 100 x 100 x 20 one; both are this rule's
-// choice.
-constexpr int ITEMS_PER_WARP = 2;
+// sweep (32 per SM; the warps draw items dynamically, so a few items each are
+// enough to balance them).  Measured on B300 (FP32 sweep): 256-512 rows best
+// on the 64 x 64 x 16 system, 1024 on the 100 x 100 x 20 one; this rule picks
+// 256 and 1024.
+constexpr int ITEMS_PER_WARP = 8;
 
 static int choose_adj_chunk(const std::vector<int32_t> &cnt, int sms) {
     const int64_t target = (int64_t)sms * 32 * ITEMS_PER_WARP;

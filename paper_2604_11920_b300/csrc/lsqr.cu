@@ -372,8 +372,16 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
     const int rps = 32 / L;                // rows per step
     const int act = rps * L;
     const int rl = lane / L, gi = lane - (lane / L) * L;
-    double ss = 0.0;
-    for (int64_t it = gw; it < a.n_adj; it += nw) {
+    // dynamic work list: lane 0 takes item indices from a counter (reset by
+    // the last block), one item ahead, so that warps that drew short items
+    // take more; the result does not depend on the assignment because each
+    // cell's sum of squares goes to the cell's slot
+    unsigned *next_item = &a.sy->count[4];
+    unsigned nxt = 0;
+    if (lane == 0) nxt = atomicAdd(next_item, 1u);
+    int64_t it = __shfl_sync(FULL, nxt, 0);
+    for (; it < a.n_adj; it = __shfl_sync(FULL, nxt, 0)) {
+        if (lane == 0) nxt = atomicAdd(next_item, 1u);
         const int h = __ldg(a.adj_item + 2 * it);
         const int q0 = __ldg(a.adj_item + 2 * it + 1);
         const int64_t c0 = __ldg(a.cell_rptr + h);
@@ -487,20 +495,17 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
                 if (k < nz)
                     css += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr, init);
             }
-            if (nch > 1) {
-                // which item finishes the cell depends on arrival order: its
-                // sum goes to the cell's slot, added in cell order at the end
-                css = warp_sum(css);
-                if (lane == 0) {
-                    a.cell_ss[h] = css;
-                    __threadfence();
-                }
-            } else {
-                ss += css;
+            // the cell's sum goes to its slot (which warp, and which of a
+            // split cell's items, finishes it depends on arrival order); the
+            // last block adds the slots in cell order
+            css = warp_sum(css);
+            if (lane == 0) {
+                a.cell_ss[h] = css;
+                __threadfence();
             }
         }
     }
-    return ss;
+    return 0.0;   // all sums went to the cell slots
 }
 
 // ------------------------------------------------------------- reductions
@@ -705,9 +710,10 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
     double tot;
     const bool last = grid_sum_last(ss, a.partial + MAXBLK, &a.sy->count[2], tot);
     if (!last) return;
-    // cells finished across several items, in cell order
+    // the blocked sweep's sums, in cell order
     const double cells = (FMT == FMT_BLK && !skip) ? block_sum_ordered(a.cell_ss, a.n_cells) : 0.0;
     if (threadIdx.x == 0) {
+        if (FMT == FMT_BLK) a.sy->count[4] = 0u;   // adjoint work counter for the next launch
         tot += cells;
         double an = skip ? alpha : sqrt(tot);
         if (!isfinite(an)) {
