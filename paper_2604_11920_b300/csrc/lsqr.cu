@@ -464,16 +464,20 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
                 const int k = lane + 32 * half;
                 if (k < nz) a.chunk_part[it * nz + k] = dot[half];
             }
-            __threadfence();
+            // the lanes' partial writes reach lane 0 through __syncwarp; its
+            // acquire-release add publishes them and, for the last item of
+            // the cell, orders the reads of the other items' partials (from
+            // L2) after their writers' adds
             __syncwarp();
             if (lane == 0) {
-                const unsigned prev = atomicAdd(a.cell_done + h, 1u);
+                unsigned prev;
+                asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;"
+                             : "=r"(prev) : "l"(a.cell_done + h) : "memory");
                 last_flag[warp] = prev == (unsigned)(nch - 1);
             }
             __syncwarp();
             finish = last_flag[warp] != 0;
             if (finish) {
-                __threadfence();
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int k = lane + 32 * half;
@@ -499,10 +503,7 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
             // split cell's items, finishes it depends on arrival order); the
             // last block adds the slots in cell order
             css = warp_sum(css);
-            if (lane == 0) {
-                a.cell_ss[h] = css;
-                __threadfence();
-            }
+            if (lane == 0) a.cell_ss[h] = css;   // read by the last block after the grid barrier
         }
     }
     return 0.0;   // all sums went to the cell slots
