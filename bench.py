@@ -374,6 +374,13 @@ def run_pdst(args, rank, world):
                             "plain_fp64": acc_plain,
                             "speedup": (acc_plain["s"] / acc_chosen["s"])
                             if acc_plain["s"] and acc_chosen["s"] else None}
+        # the column-norm form as well: the learned scaling is trained for the
+        # FP32 solve, not for the refinement sweeps
+        if args.form != "f32-blocked-colnorm":
+            acc_cn = to_accuracy("f32-blocked-colnorm")
+            accuracy_matched["f32-blocked-colnorm"] = acc_cn
+            if acc_plain["s"] and acc_cn["s"]:
+                accuracy_matched["speedup_colnorm"] = acc_plain["s"] / acc_cn["s"]
 
     # LSMR (the paper's solver) on the same sweeps: chosen form and plain FP64
     lsmr_sec = None
