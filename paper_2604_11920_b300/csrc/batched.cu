@@ -377,18 +377,19 @@ __device__ __forceinline__ void laplace4(const ST *__restrict__ x, int64_t jc, i
 // cell's last chunk (which then sums all chunks in chunk order).
 __device__ __forceinline__ bool adj_last_chunk(unsigned *cell_done, int h, int nch, int lane,
                                                int *flag) {
-    __threadfence();
+    // the lanes' partial writes reach lane 0 through __syncwarp; its
+    // acquire-release add publishes them and orders the last item's reads
+    // of the other items' partials (from L2) after their writers' adds
     __syncwarp();
     if (lane == 0) {
-        const unsigned prev = atomicAdd(cell_done + h, 1u);
+        unsigned prev;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;"
+                     : "=r"(prev) : "l"(cell_done + h) : "memory");
         *flag = prev == (unsigned)(nch - 1);
     }
     __syncwarp();
     const bool last = *flag != 0;
-    if (last) {
-        __threadfence();
-        if (lane == 0) cell_done[h] = 0u;
-    }
+    if (last && lane == 0) cell_done[h] = 0u;
     return last;
 }
 
@@ -516,16 +517,10 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
     for (int b = 0; b < 4; ++b) q[b] = __shfl_sync(FULL, ss4[b], j >> 2);
     const int cpt = j & 3;
     const double r = cpt == 0 ? q[0] : cpt == 1 ? q[1] : cpt == 2 ? q[2] : q[3];
-    if (nch > 1) {
-        // the finishing item depends on arrival order: the cell's sums go to
-        // its slots, added in cell order by k_bred
-        if (finish && lane < 16) {
-            S.cell_ss[(int64_t)h * RMAX + j] = r;
-            __threadfence();
-        }
-        return 0.0;
-    }
-    return lane < 16 ? r : 0.0;
+    // the cell's sums go to its slots, added in cell order by k_bred (which
+    // warp, and which item of a split cell, finishes the cell varies)
+    if (finish && lane < 16) S.cell_ss[(int64_t)h * RMAX + j] = r;
+    return 0.0;
 }
 
 // Adjoint work item, any RS and nz <= BNZ: lane j = right-hand side j, the two
@@ -615,42 +610,40 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
             ss += (double)v * (double)v;
         }
     }
-    if (nch > 1) {
-        if (finish && half == 0 && j < R) {
-            S.cell_ss[(int64_t)h * RMAX + j] = ss;
-            __threadfence();
-        }
-        return 0.0;
-    }
-    return ss;
+    if (finish && half == 0 && j < R) S.cell_ss[(int64_t)h * RMAX + j] = ss;
+    return 0.0;
 }
 
 // Adjoint phase: work item = a chunk of up to adj_chunk rows of one cell of
 // one system (the handle's adjoint work list).  A cell split over several
 // chunks is finished by its last chunk (chunk order sums).
+// Items are drawn dynamically from a counter (reset by k_bred), one ahead;
+// every cell's sums go to its slots, so the result does not depend on which
+// warp took which item.  The per-warp partial slots stay zero.
 template <class VT, class ST>
 __global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
-                                             int64_t nitems, int init, double *partial) {
+                                             int64_t nitems, int init, double *partial,
+                                             unsigned *next_item) {
     __shared__ int last_flag[WPB];
     WarpSum ws;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = gw; it < nitems; it += nw) {
+    unsigned nxt = 0;
+    if (lane == 0) nxt = atomicAdd(next_item, 1u);
+    for (int64_t it = __shfl_sync(FULL, nxt, 0); it < nitems; it = __shfl_sync(FULL, nxt, 0)) {
+        if (lane == 0) nxt = atomicAdd(next_item, 1u);
         const int s = find_sys(beg, nsys, it);
         const BSys<VT, ST> &S = sys[s];
         const int64_t li = it - beg[s];
-        double ss = 0.0;
         if (S.active > 0 && li < S.n_adj) {
             if (S.RS == 16 && S.nz == 16)
-                ss = adj_item16<16>(S, li, init, lane, last_flag + warp);
+                adj_item16<16>(S, li, init, lane, last_flag + warp);
             else if (S.RS == 16 && S.nz == 8)
-                ss = adj_item16<8>(S, li, init, lane, last_flag + warp);
+                adj_item16<8>(S, li, init, lane, last_flag + warp);
             else
-                ss = adj_item_any(S, li, init, lane, last_flag + warp);
+                adj_item_any(S, li, init, lane, last_flag + warp);
         }
-        ss += __shfl_xor_sync(FULL, ss, 16);
-        ws.add(ss, s, partial, gw, nw);
     }
     ws.finish(partial, nsys, gw, nw);
 }
@@ -704,13 +697,15 @@ constexpr int RED_T = 256;
 
 template <class VT, class ST>
 __global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, int G, const double *partial,
-                                                int phase, int *active_out) {
+                                                int phase, int *active_out,
+                                                unsigned *adj_counter) {
     __shared__ double part[RED_T / RMAX][RMAX];
     const int s = blockIdx.x, t = threadIdx.x, j = t % RMAX, l = t / RMAX;
     BSys<VT, ST> &S = sys[s];
     double acc = 0.0;
     for (int b = l; b < G; b += RED_T / RMAX) acc += partial[((int64_t)s * G + b) * RMAX + j];
     if (phase == PH_ADJ_INIT || phase == PH_ADJ) {
+        if (s == 0 && t == 0) *adj_counter = 0u;   // for the next adjoint launch
         const int H = S.n / S.nz;
         for (int hh = l; hh < H; hh += RED_T / RMAX) acc += __ldcg(S.cell_ss + (int64_t)hh * RMAX + j);
     }
@@ -782,7 +777,7 @@ struct BatchWork {
     int TR = 0;
     bool tuned = false;
     std::vector<DevBuf *> bufs;
-    DevBuf desc, scal, partial, fbeg, abeg, ubeg, active;
+    DevBuf desc, scal, partial, fbeg, abeg, ubeg, active, adj_ctr;
     int *h_active = nullptr;
     LsqrScalars *h_scal = nullptr;
     int64_t nf_items = 0, na_items = 0, nu_items = 0;
@@ -880,6 +875,7 @@ template <class VT, class ST> struct Batched {
             PDST_TRY(bw->scal.alloc(sizeof(LsqrScalars) * nsys * RMAX));
             PDST_TRY(bw->desc.alloc(sizeof(Sys) * nsys));
             PDST_TRY(bw->active.alloc(sizeof(int) * nsys));
+            PDST_TRY(bw->adj_ctr.alloc(sizeof(unsigned)));
             PDST_TRY(bw->abeg.alloc(sizeof(int64_t) * (nsys + 1)));
             PDST_TRY(bw->ubeg.alloc(sizeof(int64_t) * (nsys + 1)));
             PDST_CUDA(cudaMallocHost(&bw->h_active, sizeof(int) * nsys));
@@ -946,6 +942,7 @@ template <class VT, class ST> struct Batched {
         PDST_CUDA(cudaMemcpyAsync(bw->desc.p, d.data(), sizeof(Sys) * nsys, cudaMemcpyHostToDevice, s));
         for (int i = 0; i < nsys; ++i)
             PDST_CUDA(cudaMemsetAsync(bw->bufs[NB * i + 5]->p, 0, bw->bufs[NB * i + 5]->bytes, s));
+        PDST_CUDA(cudaMemsetAsync(bw->adj_ctr.p, 0, sizeof(unsigned), s));
         std::copy(init.begin(), init.end(), bw->h_scal);
         PDST_CUDA(cudaMemcpyAsync(bw->scal.p, bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX,
                                   cudaMemcpyHostToDevice, s));
@@ -957,26 +954,30 @@ template <class VT, class ST> struct Batched {
         Sys *sys = bw->desc.as<Sys>();
         double *part = bw->partial.as<double>();
         int *act = bw->active.as<int>();
+        unsigned *ctr = bw->adj_ctr.as<unsigned>();
         k_bfwd<VT, ST><<<bw->gf, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
                                              part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gf * WPB), part, PH_FWD, act);
-        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ, act);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gf * WPB), part, PH_FWD, act, ctr);
+        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part,
+                                             ctr);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
     }
 
     static pdst_status start(BatchWork *bw, int nsys, cudaStream_t s) {
         Sys *sys = bw->desc.as<Sys>();
         double *part = bw->partial.as<double>();
         int *act = bw->active.as<int>();
+        unsigned *ctr = bw->adj_ctr.as<unsigned>();
         k_binit<VT, ST><<<bw->gi, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
                                               part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gi * WPB), part, PH_INIT, act);
-        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ_INIT, act);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gi * WPB), part, PH_INIT, act, ctr);
+        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part,
+                                             ctr);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ_INIT, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
-        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act);
+        k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
         PDST_CUDA(cudaGetLastError());
         return PDST_OK;
     }
