@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pdst", "reference"], default="pdst")
-    ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "tiny", "large", "paper"], default="mid")
     ap.add_argument("--form", choices=sorted(FORMS), default=DEFAULT_FORM)
     ap.add_argument("--cpu-sample-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -102,14 +102,16 @@ def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
 
 def make_problem(name, rank):
     from paper_2604_11920_b300 import synth
-    return {"mid": synth.mid, "tiny": synth.tiny, "large": synth.large}[name](
-        seed={"mid": 1, "tiny": 0, "large": 2}[name] + 1000 * rank)
+    return {"mid": synth.mid, "tiny": synth.tiny, "large": synth.large,
+            "paper": synth.paper_shaped}[name](
+        seed={"mid": 1, "tiny": 0, "large": 2, "paper": 3}[name] + 1000 * rank)
 
 
 def workload_desc(p):
+    extra = ", bilinear node coefficients" if getattr(p, "interp", 0) else ""
     return (f"{p.nx}x{p.ny}x{p.nz} grid ({p.n} unknowns), {p.stations.shape[0]} stations, "
             f"{p.pairs.shape[0]} pairs x {p.n_periods} periods = {p.m_rows} rows, "
-            f"w={p.w}, lambda={p.lam}, tol={p.tol}")
+            f"w={p.w}, lambda={p.lam}, tol={p.tol}{extra}")
 
 
 # ------------------------------------------------------------------ clocks

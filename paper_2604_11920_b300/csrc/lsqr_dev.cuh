@@ -52,6 +52,35 @@ template <> struct Pack4<dfl> {
     }
 };
 
+// Two consecutive values (any even nz): 8-byte loads for FP32, 16 for FP64 and
+// double-float, 4 for BF16; streamed (evict-first) like the quads.
+template <class VT> struct Pack2;
+template <> struct Pack2<float> {
+    static __device__ __forceinline__ void ld(const float *p, float v[2]) {
+        const float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+};
+template <> struct Pack2<double> {
+    static __device__ __forceinline__ void ld(const double *p, double v[2]) {
+        const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+};
+template <> struct Pack2<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float v[2]) {
+        const unsigned t = __ldcs(reinterpret_cast<const unsigned *>(p));
+        v[0] = __uint_as_float(t << 16);
+        v[1] = __uint_as_float(t & 0xffff0000u);
+    }
+};
+template <> struct Pack2<dfl> {
+    static __device__ __forceinline__ void ld(const dfl *p, dfl v[2]) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = dfl(t.x, t.y); v[1] = dfl(t.z, t.w);
+    }
+};
+
 template <class VT> struct Wide { using T = VT; };
 template <> struct Wide<__nv_bfloat16> { using T = float; };
 
@@ -70,6 +99,20 @@ template <> __device__ __forceinline__ void ldx4<dfl>(const dfl *p, dfl v[4]) {
     const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
     const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
     v[0] = dfl(a.x, a.y); v[1] = dfl(a.z, a.w); v[2] = dfl(b.x, b.y); v[3] = dfl(b.z, b.w);
+}
+
+template <class ST> __device__ __forceinline__ void ldx2(const ST *p, ST v[2]);
+template <> __device__ __forceinline__ void ldx2<float>(const float *p, float v[2]) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+}
+template <> __device__ __forceinline__ void ldx2<double>(const double *p, double v[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+}
+template <> __device__ __forceinline__ void ldx2<dfl>(const dfl *p, dfl v[2]) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = dfl(t.x, t.y); v[1] = dfl(t.z, t.w);
 }
 
 __device__ __forceinline__ float ldval(const float *p) { return __ldcs(p); }

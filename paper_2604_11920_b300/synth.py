@@ -243,6 +243,19 @@ def large(seed: int = 2) -> Problem:
                         w=2.0, lam=0.05, tol=1e-6, itmax=5000, seed=seed)
 
 
+def paper_shaped(seed: int = 3) -> Problem:
+    """Stand-in for the paper's field problem (the data are not available): the
+    paper's 20 x 37 horizontal grid with 18 depth layers (13,320 unknowns), 229
+    stations (26,106 pairs) x 14 periods 1..8 s = 365,484 rows; cells of 1.5 km,
+    layers of 1 km, bent rays, Eq. 1's bilinear node coefficients, one depth
+    kernel per period (a 1-D starting model, as in the paper's first
+    iteration)."""
+    return make_problem("paper_20x37x18", 20, 37, 18, 229, np.geomspace(1.0, 8.0, 14),
+                        bend=0.15, model="blobs", noise_frac=0.02,
+                        w=2.0, lam=0.05, tol=1e-6, itmax=5000, seed=seed,
+                        dx_km=1.5, dz_km=1.0, interp=1)
+
+
 BATCH_GRIDS = ((24, 24, 8), (32, 32, 12), (48, 48, 16), (64, 64, 16))
 
 

@@ -315,3 +315,26 @@ def test_df64_form_errors(tiny):
     with pytest.raises(pdst.PdstError):
         h2.lsqr(to_dev(d), p.w, p.lam, 10, 1e-6, dtype="df64", fmt="blocked")
     h2.close()
+
+
+# ------------------------------------------------ depth counts off the quad paths
+# nz % 4 == 0 uses 4-entry vector loads; other even nz use 2-entry pairs
+# (the paper's 18 depth nodes); odd nz the scalar path.
+
+@pytest.mark.parametrize("nz", [5, 6, 10, 18])
+def test_fixed_k_iterates_other_depth_counts(nz):
+    require_cuda()
+    p = synth.make_problem(f"nz{nz}", 12, 10, nz, 14, np.geomspace(2.0, 16.0, 5), bend=0.15,
+                           model="blobs", noise_frac=0.01, w=1.0, lam=0.1, tol=1e-8,
+                           itmax=300, seed=nz, dz_km=1.0)
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    h = pdst.build_G_problem(p, dtypes=("f64", "f32", "bf16", "df64"))
+    for k in (2, 6):
+        ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=0, btol=0, conlim=0,
+                          itmax=k)
+        for dt, bar in (("f64", 1e-10), ("df64", 1e-9), ("f32", 1e-4), ("bf16", 3e-2)):
+            r = h.lsqr(to_dev(d), p.w, p.lam, k, 0.0, dtype=dt, fmt="blocked", conlim=1e300)
+            assert rel(r.m.cpu().numpy(), ref.x) < bar, (nz, k, dt)
+    h.close()
