@@ -205,6 +205,16 @@ __device__ __forceinline__ AT blk_row_quads(const VT *__restrict__ vrow, const X
     return s;
 }
 
+// floor(f / q) for a divisor fixed per row, by one high multiply with
+// m = ceil(2^32 / q) (Granlund & Montgomery, division by invariant integers):
+// f / q + f e / (q 2^32), e = m q - 2^32 < q, keeps the floor while
+// f (q - 1) < 2^32, far above any row's entry count.
+struct DivQ {
+    uint32_t q, m;
+    __device__ __forceinline__ explicit DivQ(uint32_t q_) : q(q_), m(q_ > 1u ? 0xFFFFFFFFu / q_ + 1u : 0u) {}
+    __device__ __forceinline__ uint32_t div(uint32_t f) const { return q > 1u ? __umulhi(f, m) : f; }
+};
+
 // Same for any nz % 4 == 0 (run and quad from a run-time division).
 template <class VT, class AT, class XT>
 __device__ __forceinline__ AT blk_row_quads_rt(const VT *__restrict__ vrow,
@@ -214,7 +224,7 @@ __device__ __forceinline__ AT blk_row_quads_rt(const VT *__restrict__ vrow,
     const uint32_t q = nz >> 2, nquad = nrun * q;
     AT s = 0;
     for (uint32_t f = hl; f < nquad; f += 16u) {
-        const uint32_t run = f / q;
+        const uint32_t run = f / q;   // (the high-multiply division measured slower here)
         const int h = __ldg(cells_row + run);
         typename Wide<VT>::T vv[4];
         XT xx[4];
@@ -243,6 +253,7 @@ __device__ __forceinline__ AT blk_row_pairs_rt(const VT *__restrict__ vrow,
                                                uint32_t nrun, uint32_t nz, int hl) {
     constexpr int UP = 4;
     const uint32_t q = nz >> 1, npair = nrun * q;
+    const DivQ dq(q);
     AT s = 0;
     for (uint32_t base = 0; base < npair; base += 16u * UP) {
         int h[UP];
@@ -250,7 +261,7 @@ __device__ __forceinline__ AT blk_row_pairs_rt(const VT *__restrict__ vrow,
 #pragma unroll
         for (int u = 0; u < UP; ++u) {
             const uint32_t f = base + hl + 16u * u;
-            const uint32_t run = f / q;
+            const uint32_t run = dq.div(f);
             off[u] = 2u * (f - run * q);
             h[u] = f < npair ? __ldg(cells_row + run) : -1;
         }
@@ -357,12 +368,13 @@ __device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, S
     }
     if ((nz & 1u) == 0u) return fwd_rows_halfwarp<VT, ST, -1>(a, ia, cu, gw, nw, lane);
     double ss = 0.0;
+    const DivQ dq(nz);
     for (int64_t r = gw; r < a.m; r += nw) {
         const int64_t e0 = __ldg(a.row_cptr + r), e1 = __ldg(a.row_cptr + r + 1);
         const uint32_t len = (uint32_t)(e1 - e0) * nz;
         AT part = 0;
         for (uint32_t rel = lane; rel < len; rel += 32u) {
-            const uint32_t ee = rel / nz, k = rel - ee * nz;
+            const uint32_t ee = dq.div(rel), k = rel - ee * nz;
             const int h = __ldg(a.row_cells + e0 + ee);
             part += (AT)widen(a.val[e0 * (int64_t)nz + rel]) * (AT)__ldg(a.vsc + (int64_t)h * nz + k);
         }
@@ -374,6 +386,20 @@ __device__ __forceinline__ double fwd_rows_blk(const OpArgs<VT, ST> &a, ST ia, S
         }
     }
     return ss;
+}
+
+// Entries per lane of the blocked adjoint for a depth count: 4 (nz % 4 == 0),
+// 6 (nz % 6 == 0, e.g. 18 depth nodes: 3 lanes per row, measured 1.45x
+// faster than pairs at nz = 18), 2 (other even nz), 1.  G = 2 and G = 1 run
+// as kernels of their own (measured 9 % and 14 % faster on B300 than inside
+// the kernel that holds every group); G = 4 and 6 share G_ANY, which picks
+// the group at run time (equal or faster for them).
+constexpr int G_ANY = 0;
+__host__ __device__ constexpr int adj_group(int nz) {
+    return (nz & 3) == 0 && nz <= 64   ? 4
+           : nz % 6 == 0 && nz <= 96   ? 6
+           : (nz & 1) == 0 && nz <= 64 ? 2
+                                       : 1;
 }
 
 // Final value of column j of the adjoint sweep from its G^T u dot product:
@@ -735,10 +761,14 @@ static __device__ void sweep_step(LsqrScalars *base, LsqrScalars *ls, int L, dou
 // v-bar <- (A^T u-bar)/beta - (beta/alpha) v-bar;  alpha <- ||v-bar||, then
 // the scalar recurrence (or its initialisation when init != 0).  With BF16
 // values three blocks per SM (up to 85 registers) measured faster than four.
-template <class VT, class ST, int FMT>
+template <class VT, class ST, int FMT, int G>
 __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, ST> a, int init) {
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
+    if (FMT == FMT_BLK && G != G_ANY && adj_group(a.nz) != G) {   // another depth count
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->err = sc->done = 1;
+        return;
+    }
     using AT = ST;
     const double alpha = sc->alpha, beta = sc->beta;
     const bool skip = !init && !(beta > 0.0);
@@ -751,15 +781,16 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
     double ss = 0.0;
     if (!skip) {
         if constexpr (FMT == FMT_BLK) {
-            ss = (a.nz & 3) == 0 && a.nz <= 64
-                     ? adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane)
-                 // nz % 6 == 0 (e.g. 18 depth nodes): three pairs per lane, 3 lanes per
-                 // row (measured 1.45x faster than one pair per lane at nz = 18)
-                 : a.nz % 6 == 0 && a.nz <= 96
-                     ? adj_cells_chunked<VT, ST, 6>(a, ib, cv, wsm, lamr, init, gw, nw, lane)
-                 : (a.nz & 1) == 0 && a.nz <= 64
-                     ? adj_cells_chunked<VT, ST, 2>(a, ib, cv, wsm, lamr, init, gw, nw, lane)
-                     : adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+            if constexpr (G == G_ANY) {
+                switch (adj_group(a.nz)) {
+                case 4: ss = adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
+                case 6: ss = adj_cells_chunked<VT, ST, 6>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
+                case 2: ss = adj_cells_chunked<VT, ST, 2>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
+                default: ss = adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+                }
+            } else {
+                ss = adj_cells_chunked<VT, ST, (G > 0 ? G : 1)>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+            }
         } else {
             for (int64_t j = gw; j < a.n; j += nw) {
                 AT dot = dot_elem<VT, AT, ST>(a.col_ptr, a.row_idx, a.valT, a.ubar, j, lane);
@@ -1026,6 +1057,16 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     return a;
 }
 
+// The blocked adjoint kernel for a handle's depth count.
+template <class VT, class ST, int FMT> static auto adj_kernel(int nz) {
+    if constexpr (FMT == FMT_BLK) {
+        const int g = adj_group(nz);
+        if (g == 2) return k_adj<VT, ST, FMT, 2>;
+        if (g == 1) return k_adj<VT, ST, FMT, 1>;
+    }
+    return k_adj<VT, ST, FMT, G_ANY>;
+}
+
 template <class K> static unsigned persistent_grid(K kernel, int device, int64_t work_items) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LT, 0);
@@ -1066,14 +1107,14 @@ template <class VT, class ST, int FMT> struct Solver {
         w->M = M;
         // warp-per-row kernels: items = rows * 32 threads
         w->grid_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
-        w->grid_cols = persistent_grid(k_adj<VT, ST, FMT>, h->device, (int64_t)h->n * 32);
+        w->grid_cols = persistent_grid(adj_kernel<VT, ST, FMT>(h->nz), h->device, (int64_t)h->n * 32);
         w->grid_vec = persistent_grid(k_upd<ST>, h->device, h->n);
         return PDST_OK;
     }
 
     static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
         k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
-        k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+        adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
     }
 
@@ -1087,7 +1128,7 @@ template <class VT, class ST, int FMT> struct Solver {
             cudaEventRecord(ev[4 * i], s);
             k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
             cudaEventRecord(ev[4 * i + 1], s);
-            k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+            adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
             cudaEventRecord(ev[4 * i + 2], s);
             k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
             cudaEventRecord(ev[4 * i + 3], s);
@@ -1123,7 +1164,7 @@ template <class VT, class ST, int FMT> struct Solver {
         unsigned ginit = persistent_grid(k_init<ST>, h->device, w->M);
         k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, baug, a.ubar, a.x, a.wv, a.partial, a.sc,
                                         a.sy);
-        k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
+        adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 1);
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
         PDST_CUDA(cudaGetLastError());
         rs.launches += 3;
@@ -1567,7 +1608,7 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
     const unsigned ginit = persistent_grid(k_init<ST>, h->device, w->M);
     k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, nullptr, a.ubar, a.x, a.wv, a.partial,
                                     a.sc, a.sy);
-    k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 1);
+    adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 1);
     k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.lam_sc,
                                       w->sw_cnt.as<unsigned>());
     PDST_CUDA(cudaGetLastError());
@@ -1580,7 +1621,7 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
         if (c.done || c.istop || c.err || c.itn >= c.itmax) break;
         for (int i = 0; i < kblock; ++i) {
             k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
-            k_adj<VT, ST, FMT><<<w->grid_cols, LT, 0, s>>>(a, 0);
+            adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
             k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(),
                                               a.lam_sc, w->sw_cnt.as<unsigned>());
         }
@@ -1925,7 +1966,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     a.sc = sc;
     a.sy = sy;
     const unsigned g_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
-    const unsigned g_cols = persistent_grid(k_adj<VT, ST, FMT>, h->device, (int64_t)h->n * 32);
+    const unsigned g_cols = persistent_grid(adj_kernel<VT, ST, FMT>(h->nz), h->device, (int64_t)h->n * 32);
     const unsigned g_vec = persistent_grid(k_upd<ST>, h->device, h->n);
     const unsigned g_init = persistent_grid(k_init<ST>, h->device, M);
 
@@ -1938,7 +1979,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     LsqrScalars hs = init;
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
     k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, nullptr, ubar, x, wv, partial, sc, sy);
-    k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 1);
+    adj_kernel<VT, ST, FMT>(h->nz)<<<g_cols, LT, 0, s>>>(a, 1);
     k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
     PDST_CUDA(cudaGetLastError());
     launches += 3;
@@ -1948,7 +1989,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
         if (fin.done || fin.istop || fin.itn >= fin.itmax) break;
         for (int i = 0; i < kblock; ++i) {
             k_fwd<VT, ST, FMT><<<g_rows, LT, 0, s>>>(a);
-            k_adj<VT, ST, FMT><<<g_cols, LT, 0, s>>>(a, 0);
+            adj_kernel<VT, ST, FMT>(h->nz)<<<g_cols, LT, 0, s>>>(a, 0);
             k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
         }
         PDST_CUDA(cudaGetLastError());
