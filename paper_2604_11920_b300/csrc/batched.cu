@@ -702,12 +702,30 @@ __global__ void __launch_bounds__(RED_T) k_bred(BSys<VT, ST> *sys, int G, const 
     __shared__ double part[RED_T / RMAX][RMAX];
     const int s = blockIdx.x, t = threadIdx.x, j = t % RMAX, l = t / RMAX;
     BSys<VT, ST> &S = sys[s];
+    // both sums take their terms in index order, the loads issued eight at a
+    // time (one L2 round trip per eight terms); slots past the end add +0.0,
+    // which leaves these sums of squares unchanged bit for bit
+    constexpr int LS = RED_T / RMAX;
     double acc = 0.0;
-    for (int b = l; b < G; b += RED_T / RMAX) acc += partial[((int64_t)s * G + b) * RMAX + j];
+    for (int b = l; b < G; b += 8 * LS) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = b + u * LS < G ? partial[((int64_t)s * G + b + u * LS) * RMAX + j] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
     if (phase == PH_ADJ_INIT || phase == PH_ADJ) {
         if (s == 0 && t == 0) *adj_counter = 0u;   // for the next adjoint launch
         const int H = S.n / S.nz;
-        for (int hh = l; hh < H; hh += RED_T / RMAX) acc += __ldcg(S.cell_ss + (int64_t)hh * RMAX + j);
+        for (int hh = l; hh < H; hh += 8 * LS) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = hh + u * LS < H ? __ldcg(S.cell_ss + (int64_t)(hh + u * LS) * RMAX + j) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += v[u];
+        }
     }
     part[l][j] = acc;
     __syncthreads();

@@ -648,6 +648,23 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
 
 // ------------------------------------------------------------- reductions
 
+// v[i0] + v[i0 + st] + v[i0 + 2 st] + ... (i < n), added in that order, the
+// loads issued eight at a time: one L2 round trip per eight terms instead of
+// one per term (the last block's sums of block partials and cell slots were
+// latency chains of up to 40 round trips, ~20 us per launch).  Slots past n
+// add +0.0, which leaves a sum of squares unchanged bit for bit.
+__device__ __forceinline__ double strided_sum(const double *v, int64_t n, int i0, int st) {
+    double s = 0.0;
+    for (int64_t i = i0; i < n; i += 8 * (int64_t)st) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = i + (int64_t)u * st < n ? __ldcg(v + i + (int64_t)u * st) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += t[u];
+    }
+    return s;
+}
+
 // Block sum of v, then the block that finishes last sums the per-block
 // partials in index order.  Returns true in that block; `total` is valid in
 // its first warp.
@@ -672,7 +689,7 @@ __device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigne
     __threadfence();
     double s = 0.0;
     if (warp == 0) {
-        for (int i = lane; i < (int)gridDim.x; i += 32) s += __ldcg(partial + i);
+        s = strided_sum(partial, (int64_t)gridDim.x, lane, 32);
         s = warp_sum(s);
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -685,8 +702,7 @@ __device__ __forceinline__ bool grid_sum_last(double v, double *partial, unsigne
 __device__ __forceinline__ double block_sum_ordered(const double *v, int64_t n) {
     __shared__ double red2[LT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(v + i);
+    double s = strided_sum(v, n, (int)threadIdx.x, (int)blockDim.x);
     s = warp_sum(s);
     if (lane == 0) red2[warp] = s;
     __syncthreads();
@@ -783,36 +799,43 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_fwd(OpArgs<VT, 
     }
 }
 
-// Damping sweep: u and v (and so alpha and beta) do not depend on the
-// damping, which enters only the scalar recurrence.  After alpha_{k+1} is
-// known, advance the recurrence of every damping value still running; the
-// bidiagonalisation stops (base istop) once all have stopped.
 static __device__ void sweep_step(LsqrScalars *base, LsqrScalars *ls, int L, double an, int init) {
-    int running = 0;
-    for (int l = 0; l < L; ++l) {
-        LsqrScalars *c = ls + l;
-        if (init) {
-            c->beta = base->beta;
-            c->bnorm = base->bnorm;
-            c->rnorm = base->rnorm;
-            c->phibar = base->phibar;
-            c->alpha = an;
-            c->rhobar = an;
-            c->arnorm = an * base->beta;
-            c->pending = 2;
-            if (!(c->arnorm > 0.0)) c->done = 1;
-        } else if (!(c->done | c->istop)) {
-            c->beta = base->beta;
-            lsqr_step(c, an);
+    // the values are independent: lane 0 of warp l advances values l, l + 8, ...
+    // (their FP64 chains overlap), then thread 0 counts the running ones
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int l = warp; l < L; l += (int)(blockDim.x >> 5)) {
+            LsqrScalars *c = ls + l;
+            if (init) {
+                c->beta = base->beta;
+                c->bnorm = base->bnorm;
+                c->rnorm = base->rnorm;
+                c->phibar = base->phibar;
+                c->alpha = an;
+                c->rhobar = an;
+                c->arnorm = an * base->beta;
+                c->pending = 2;
+                if (!(c->arnorm > 0.0)) c->done = 1;
+            } else if (!(c->done | c->istop)) {
+                c->beta = base->beta;
+                lsqr_step(c, an);
+            }
         }
-        if (c->err) base->err = 1;
-        running += !(c->done | c->istop);
     }
-    base->alpha = an;
-    if (!init) base->itn += 1;
-    if (!running) {
-        if (init) base->done = 1;
-        else base->istop = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int running = 0;
+        for (int l = 0; l < L; ++l) {
+            const LsqrScalars *c = ls + l;
+            if (c->err) base->err = 1;
+            running += !(c->done | c->istop);
+        }
+        base->alpha = an;
+        if (!init) base->itn += 1;
+        if (!running) {
+            if (init) base->done = 1;
+            else base->istop = 1;
+        }
     }
 }
 
@@ -861,6 +884,18 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
     if (!last) return;
     // the blocked sweep's sums, in cell order
     const double cells = (FMT == FMT_BLK && !skip) ? block_sum_ordered(a.cell_ss, a.n_cells) : 0.0;
+    if (a.n_lam > 0) {
+        // damping sweep: one recurrence per damping value, one warp each
+        __shared__ double an_s;
+        if (threadIdx.x == 0) {
+            if (FMT == FMT_BLK) a.sy->count[4] = 0u;   // adjoint work counter for the next launch
+            an_s = skip ? alpha : sqrt(tot + cells);
+            if (!isfinite(an_s)) sc->err = sc->done = 1;
+        }
+        __syncthreads();
+        if (isfinite(an_s)) sweep_step(sc, a.lam_sc, a.n_lam, an_s, init);
+        return;
+    }
     if (threadIdx.x == 0) {
         if (FMT == FMT_BLK) a.sy->count[4] = 0u;   // adjoint work counter for the next launch
         tot += cells;
@@ -870,9 +905,7 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
             sc->done = 1;
             return;
         }
-        if (a.n_lam > 0) {
-            sweep_step(sc, a.lam_sc, a.n_lam, an, init);
-        } else if (init) {
+        if (init) {
             sc->alpha = an;
             sc->rhobar = an;
             sc->arnorm = an * beta;
