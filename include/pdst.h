@@ -197,8 +197,10 @@ typedef struct {
     int32_t kernel_launches; /* kernels this call launched (graph nodes included) */
     int32_t profiled_iters;  /* iterations covered by the *_ms fields (profile = 1) */
     double fwd_ms;   /* total device time of the forward kernel A v (profile = 1) */
-    double adj_ms;   /* total device time of the adjoint kernel A^T u + recurrence */
-    double upd_ms;   /* total device time of the x/w update kernel */
+    double adj_ms;   /* total device time of the adjoint kernel A^T u (+ its norm) */
+    double upd_ms;   /* total device time of the x/w update and the scalar step of the
+                        recurrence (one-warp kernel; in graph replay it runs beside the
+                        forward) */
     int32_t sweeps;  /* refinement sweeps performed (0 without refinement); iters is the
                         total over all sweeps and the other fields describe the last one */
     int32_t reserved;

@@ -97,8 +97,11 @@ struct LsqrScalars {
     double betadd, betad, rhod_prev, tautilde_prev, thetatilde, zeta_prev, dsum;
     double anorm2, rbar_max, rbar_min;
     double t3;                     // LSMR: h = v - t3 h (t1: h-bar, t2: x)
+    double alpha_next;             // alpha_{i+1} from the adjoint sweep (the forward's scale)
+    double beta_next;              // beta_{i+2} from a forward that ran beside a pending step
     int32_t itn, itmax, istop, pending, done, err;
     int32_t method;                // 0 LSQR, 1 LSMR
+    int32_t step_pending;          // 1: the adjoint left its scalar step to k_step
 };
 
 // "Last block" counters of the reduction kernels.

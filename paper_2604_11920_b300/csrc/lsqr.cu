@@ -3,14 +3,20 @@
 // the solver of the paper's least-squares module ("Solver for the
 // Large-scale Linear System"; the paper names LSQR beside LSMR).
 //
-// One iteration is three kernels:
+// One iteration is four kernels:
+//   k_step the FP64 scalar recurrence of the previous adjoint (rotations, norm
+//          estimates, stopping rules), one warp, run beside k_fwd, which needs
+//          only alpha and beta (on B300 the step's chain of dependent FP64
+//          operations takes ~16 us; at the end of k_adj it was ~14 % of a
+//          64 x 64 x 16 adjoint sweep)
 //   k_fwd  u-bar <- A v - alpha u and beta = ||u-bar||   (G rows: warp per CSR
 //          row, gather of v; L rows: 7-point stencil, thread per column)
+//   k_upd  x += t1 w, w = v + t2 w in FP64 and ||w||^2 with the step's
+//          coefficients, which its last block publishes
 //   k_adj  v-bar <- A^T u - beta v and alpha = ||v-bar|| (warp per CSC column,
-//          gather of u; the stencil term added by the same warp); the last
-//          block to finish advances the FP64 scalar recurrence (rotations,
-//          norm estimates, stopping rules)
-//   k_upd  x += t1 w, w = v + t2 w in FP64 and ||w||^2
+//          gather of u; the stencil term added by the same warp); its last
+//          block leaves the scalar step pending for the next k_step (the
+//          damping sweep advances its recurrences there instead)
 // Both products are gathers (no atomics).  Vectors are never normalised in
 // place: u-bar and v-bar are kept with their norms and the 1/beta, 1/alpha
 // factors are folded into the next product, so each Golub-Kahan step is one
@@ -67,6 +73,7 @@ template <class VT, class ST> struct OpArgs {
     double *x, *wv;           // n, FP64
     double *partial;          // 3 x MAXBLK
     LsqrScalars *sc;
+    LsqrScalars *sc_stage;    // the deferred scalar step's copy (k_step; published by k_upd)
     LsqrSync *sy;
 };
 
@@ -746,6 +753,30 @@ __global__ void __launch_bounds__(LT) k_init(int64_t m, int64_t M, int32_t n,
     }
 }
 
+// Copy of the scalars by the calling threads (8-byte words).
+__device__ __forceinline__ void copy_scalars(LsqrScalars *dst, const LsqrScalars *src, int t,
+                                             int nt) {
+    static_assert(sizeof(LsqrScalars) % 8 == 0, "LsqrScalars: whole 8-byte words");
+    for (int i = t; i < (int)(sizeof(LsqrScalars) / 8); i += nt)
+        reinterpret_cast<unsigned long long *>(dst)[i] =
+            reinterpret_cast<const unsigned long long *>(src)[i];
+}
+
+// The scalar step the adjoint left pending (alpha_new = alpha_{i+1}), one
+// warp, launched beside the next forward sweep: its chain of dependent FP64
+// operations (B300's FP64 pipe is narrow) took ~17 us at the end of every
+// adjoint sweep.  It works on a staging copy, since the forward reads the
+// scalars meanwhile; k_upd, which follows both, publishes it.
+__global__ void __launch_bounds__(32) k_step(const LsqrScalars *sc, LsqrScalars *stage) {
+    if (!sc->step_pending || (sc->done | sc->istop)) return;
+    copy_scalars(stage, sc, threadIdx.x, 32);
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (stage->method == 1) lsmr_step(stage, stage->alpha_next);
+        else lsqr_step(stage, stage->alpha_next);
+    }
+}
+
 // u-bar <- (A v-bar)/alpha - (alpha/beta) u-bar;  beta <- ||u-bar||.  BF16
 // values: three blocks per SM, as in the adjoint.
 template <class VT, class ST, int FMT>
@@ -753,7 +784,9 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_fwd(OpArgs<VT, 
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
     using AT = ST;
-    const double alpha = sc->alpha, beta = sc->beta;
+    // alpha_{i+1} and beta_{i+1}: the scalar step of iteration i (k_step, run
+    // beside this kernel) is not needed here
+    const double alpha = sc->alpha_next, beta = sc->beta;
     const AT ia = alpha > 0.0 ? (AT)(1.0 / alpha) : (AT)0;
     const AT cu = beta > 0.0 ? (AT)(alpha / beta) : (AT)0;
     const AT wsm = (AT)sc->w_smooth, lamr = (AT)sc->lam_rows;
@@ -795,7 +828,11 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_fwd(OpArgs<VT, 
             sc->err = 1;
             sc->done = 1;
         }
-        sc->beta = b;
+        // a pending step still reads beta_{i+1}: k_upd moves beta_next in
+        // (the flag is read here, not kept live through the sweep: one more
+        // live register cost the FP32 forward up to 4 % at 64 registers)
+        if (sc->step_pending) sc->beta_next = b;
+        else sc->beta = b;
     }
 }
 
@@ -891,6 +928,7 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
             if (FMT == FMT_BLK) a.sy->count[4] = 0u;   // adjoint work counter for the next launch
             an_s = skip ? alpha : sqrt(tot + cells);
             if (!isfinite(an_s)) sc->err = sc->done = 1;
+            sc->alpha_next = an_s;
         }
         __syncthreads();
         if (isfinite(an_s)) sweep_step(sc, a.lam_sc, a.n_lam, an_s, init);
@@ -905,6 +943,7 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
             sc->done = 1;
             return;
         }
+        sc->alpha_next = an;
         if (init) {
             sc->alpha = an;
             sc->rhobar = an;
@@ -912,10 +951,8 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
             sc->pending = 2;
             if (sc->method == 1) lsmr_init(sc, an);
             if (!(sc->arnorm > 0.0)) sc->done = 1;
-        } else if (sc->method == 1) {
-            lsmr_step(sc, an);
         } else {
-            lsqr_step(sc, an);
+            sc->step_pending = 1;   // the scalar step runs in k_step
         }
     }
 }
@@ -934,21 +971,51 @@ __device__ __forceinline__ void lsqr_xw(double vbar_j, double ia, double t1, dou
     }
 }
 
+// Publication of a deferred step (k_step's copy) by one block: everything but
+// beta, which the forward that ran beside k_step left in beta_next, and the
+// forward's error flags, which are kept.
+__device__ __forceinline__ void publish_step(LsqrScalars *sc, const LsqrScalars *stage) {
+    __shared__ double bnext;
+    __shared__ int err, done;
+    if (threadIdx.x == 0) {
+        bnext = sc->beta_next;
+        err = sc->err;
+        done = sc->done;
+    }
+    __syncthreads();
+    copy_scalars(sc, stage, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sc->beta = bnext;
+        sc->err |= err;
+        sc->done |= done;
+        sc->step_pending = 0;
+    }
+    __syncthreads();
+}
+
 // LSQR: x += t1 w; w = v + t2 w (FP64), v = v-bar/alpha;  ||w||^2.
 // LSMR (wv holds h): hbar = h - t1 hbar; x += t2 hbar; h = v - t3 h;  ||x||^2,
-// then the stopping tests on the new ||x|| (last block).
+// then the stopping tests on the new ||x|| (last block).  The coefficients
+// come from k_step's copy when a deferred step is pending; the last block
+// (block 0 when there is no update) then publishes it.
 template <class ST>
 __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vbar, double *x,
                                             double *wv, double *hbar, double *partial,
-                                            LsqrScalars *sc, LsqrSync *sy) {
-    const int pend = sc->pending;
-    if (!pend) return;
-    const double alpha = sc->alpha;
+                                            LsqrScalars *sc, LsqrScalars *stage, LsqrSync *sy) {
+    const bool pub = sc->step_pending != 0;
+    const LsqrScalars *src = pub ? stage : sc;
+    const int pend = src->pending;
+    if (!pend) {
+        if (pub && blockIdx.x == 0) publish_step(sc, stage);
+        return;
+    }
+    const double alpha = src->alpha;
     const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-    const double t1 = sc->t1, t2 = sc->t2;
+    const double t1 = src->t1, t2 = src->t2;
     double ss = 0.0;
-    if (sc->method == 1) {
-        const double t3 = sc->t3;
+    if (src->method == 1) {
+        const double t3 = src->t3;
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
              j += (int64_t)gridDim.x * blockDim.x) {
             const double v = (double)vbar[j] * ia;
@@ -967,10 +1034,13 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
             ss += xj * xj;
         }
         double tot;
-        if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot) && threadIdx.x == 0) {
-            sc->xnorm = sqrt(tot);
-            if (pend != 2) stop_tests(sc);
-            sc->pending = 0;
+        if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot)) {
+            if (pub) publish_step(sc, stage);
+            if (threadIdx.x == 0) {
+                sc->xnorm = sqrt(tot);
+                if (pend != 2) stop_tests(sc);
+                sc->pending = 0;
+            }
         }
         return;
     }
@@ -983,9 +1053,12 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
         ss = __fma_rn(w, w, ss);
     }
     double tot;
-    if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot) && threadIdx.x == 0) {
-        sc->wnorm2 = tot;
-        sc->pending = 0;
+    if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot)) {
+        if (pub) publish_step(sc, stage);
+        if (threadIdx.x == 0) {
+            sc->wnorm2 = tot;
+            sc->pending = 0;
+        }
     }
 }
 
@@ -1095,10 +1168,15 @@ struct LsqrWork {
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
     std::map<int, cudaGraphExec_t> graphs;   // key: kblock
+    cudaStream_t side = nullptr;             // k_step beside k_fwd
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~LsqrWork() {
         for (auto &g : graphs)
             if (g.second) cudaGraphExecDestroy(g.second);
         if (h_scal) cudaFreeHost(h_scal);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -1140,6 +1218,7 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
         a.hbar = w->hbar.as<double>();
         a.partial = w->partial.as<double>();
         a.sc = w->scal.as<LsqrScalars>();
+        a.sc_stage = a.sc + 1;
         a.sy = w->sync.as<LsqrSync>();
         a.chunk_part = w->chunk_part.as<ST>();
         a.cell_done = w->cell_done.as<unsigned>();
@@ -1170,6 +1249,16 @@ template <class K> static unsigned persistent_grid(K kernel, int device, int64_t
     return (unsigned)g;
 }
 
+// The forward's grid: one block short of a full persistent grid, so that
+// k_step (one warp, launched beside it) always finds a free slot.
+template <class K> static unsigned fwd_grid(K kernel, int device, int64_t work_items) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LT, 0);
+    const unsigned g = persistent_grid(kernel, device, work_items);
+    const int64_t full = (int64_t)num_sms(device) * (per_sm < 1 ? 1 : per_sm);
+    return (g > 1 && (int64_t)g >= full) ? g - 1 : g;
+}
+
 struct RunStats {
     int launches = 0, profiled_iters = 0;
     double fwd_ms = 0, adj_ms = 0, upd_ms = 0;
@@ -1188,7 +1277,7 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_TRY(w->wv.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
         PDST_TRY(w->hbar.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
         PDST_TRY(w->partial.alloc(sizeof(double) * 3 * MAXBLK));
-        PDST_TRY(w->scal.alloc(sizeof(LsqrScalars)));
+        PDST_TRY(w->scal.alloc(2 * sizeof(LsqrScalars)));   // scalars, k_step's copy
         PDST_TRY(w->sync.alloc(sizeof(LsqrSync)));
         PDST_TRY(w->chunk_part.alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz, 1)));
         PDST_TRY(w->cell_done.alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
@@ -1197,44 +1286,66 @@ template <class VT, class ST, int FMT> struct Solver {
         if (!w->h_scal) PDST_CUDA(cudaMallocHost(&w->h_scal, sizeof(LsqrScalars)));
         w->M = M;
         // warp-per-row kernels: items = rows * 32 threads
-        w->grid_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
+        w->grid_rows = fwd_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
+        if (!w->side) PDST_CUDA(cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking));
+        if (!w->ev_fork) PDST_CUDA(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+        if (!w->ev_join) PDST_CUDA(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
         w->grid_cols = persistent_grid(adj_kernel<VT, ST, FMT>(h->nz), h->device, (int64_t)h->n * 32);
         w->grid_vec = persistent_grid(k_upd<ST>, h->device, h->n);
         return PDST_OK;
     }
 
+    // One iteration: the previous adjoint's scalar step (k_step, on a side
+    // stream) beside the forward, which needs only alpha_{i+1}; then the x/w
+    // update of that step (it reads v-bar_{i+1}, as the forward does); then
+    // the adjoint, which overwrites v-bar.
+    static void fork_step(LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
+        cudaEventRecord(w->ev_fork, s);
+        cudaStreamWaitEvent(w->side, w->ev_fork, 0);
+        k_step<<<1, 32, 0, w->side>>>(a.sc, a.sc_stage);
+        cudaEventRecord(w->ev_join, w->side);
+    }
     static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
+        fork_step(w, a, s);
         k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
+        cudaStreamWaitEvent(s, w->ev_join, 0);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc,
+                                             a.sc_stage, a.sy);
         adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
-        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
     }
 
     // Per-kernel device time of `iters` plain-launched iterations, each kernel
-    // bracketed by CUDA events on the launching stream.
+    // bracketed by CUDA events on the launching stream.  k_step runs in line
+    // here (so the forward's time is its own) and counts with the update.
     static pdst_status profiled_block(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a,
                                       int iters, cudaStream_t s, RunStats &rs) {
-        std::vector<cudaEvent_t> ev(4 * (size_t)iters);
+        constexpr int E = 5;
+        std::vector<cudaEvent_t> ev(E * (size_t)iters);
         for (auto &e : ev) PDST_CUDA(cudaEventCreate(&e));
         for (int i = 0; i < iters; ++i) {
-            cudaEventRecord(ev[4 * i], s);
+            cudaEventRecord(ev[E * i], s);
+            k_step<<<1, 32, 0, s>>>(a.sc, a.sc_stage);
+            cudaEventRecord(ev[E * i + 1], s);
             k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
-            cudaEventRecord(ev[4 * i + 1], s);
+            cudaEventRecord(ev[E * i + 2], s);
+            k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc,
+                                                 a.sc_stage, a.sy);
+            cudaEventRecord(ev[E * i + 3], s);
             adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
-            cudaEventRecord(ev[4 * i + 2], s);
-            k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
-            cudaEventRecord(ev[4 * i + 3], s);
+            cudaEventRecord(ev[E * i + 4], s);
         }
         PDST_CUDA(cudaGetLastError());
         PDST_CUDA(cudaStreamSynchronize(s));
-        rs.launches += 3 * iters;
+        rs.launches += 4 * iters;
         for (int i = 0; i < iters; ++i) {
-            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            cudaEventElapsedTime(&t0, ev[4 * i], ev[4 * i + 1]);
-            cudaEventElapsedTime(&t1, ev[4 * i + 1], ev[4 * i + 2]);
-            cudaEventElapsedTime(&t2, ev[4 * i + 2], ev[4 * i + 3]);
-            rs.fwd_ms += t0;
-            rs.adj_ms += t1;
-            rs.upd_ms += t2;
+            float ts = 0.f, tf = 0.f, tu = 0.f, ta = 0.f;
+            cudaEventElapsedTime(&ts, ev[E * i], ev[E * i + 1]);
+            cudaEventElapsedTime(&tf, ev[E * i + 1], ev[E * i + 2]);
+            cudaEventElapsedTime(&tu, ev[E * i + 2], ev[E * i + 3]);
+            cudaEventElapsedTime(&ta, ev[E * i + 3], ev[E * i + 4]);
+            rs.fwd_ms += tf;
+            rs.adj_ms += ta;
+            rs.upd_ms += ts + tu;
         }
         for (auto &e : ev) cudaEventDestroy(e);
         return PDST_OK;
@@ -1256,7 +1367,8 @@ template <class VT, class ST, int FMT> struct Solver {
         k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, baug, a.ubar, a.x, a.wv, a.partial, a.sc,
                                         a.sy);
         adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 1);
-        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc, a.sy);
+        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc,
+                                             a.sc_stage, a.sy);
         PDST_CUDA(cudaGetLastError());
         rs.launches += 3;
 
@@ -1294,11 +1406,11 @@ template <class VT, class ST, int FMT> struct Solver {
                 PDST_TRY(profiled_block(h, w, a, 1, s, rs));
             } else if (exec) {
                 PDST_CUDA(cudaGraphLaunch(exec, s));
-                rs.launches += 3 * kblock;
+                rs.launches += 4 * kblock;
             } else {
                 for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, s);
                 PDST_CUDA(cudaGetLastError());
-                rs.launches += 3 * kblock;
+                rs.launches += 4 * kblock;
             }
         }
         k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out, accumulate ? 1 : 0);
@@ -2014,7 +2126,7 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Bytes of scratch one solve needs, in the carving order used below.
 static size_t noalloc_need(int64_t M, int64_t n, size_t st, int64_t chunk_vals, int64_t H) {
-    return align256(sizeof(LsqrScalars)) + align256(sizeof(LsqrSync)) +
+    return align256(2 * sizeof(LsqrScalars)) + align256(sizeof(LsqrSync)) +
            align256(sizeof(double) * 3 * MAXBLK) + align256(st * M) + 2 * align256(st * n) +
            2 * align256(sizeof(double) * n) + align256(st * chunk_vals) +
            align256(sizeof(unsigned) * H) + align256(sizeof(double) * H);
@@ -2032,7 +2144,7 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
         off += align256(bytes);
         return p;
     };
-    auto *sc = reinterpret_cast<LsqrScalars *>(carve(sizeof(LsqrScalars)));
+    auto *sc = reinterpret_cast<LsqrScalars *>(carve(2 * sizeof(LsqrScalars)));   // + k_step's copy
     auto *sy = reinterpret_cast<LsqrSync *>(carve(sizeof(LsqrSync)));
     auto *partial = reinterpret_cast<double *>(carve(sizeof(double) * 3 * MAXBLK));
     auto *ubar = reinterpret_cast<ST *>(carve(sizeof(ST) * M));
@@ -2055,8 +2167,9 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     a.wv = wv;
     a.partial = partial;
     a.sc = sc;
+    a.sc_stage = sc + 1;
     a.sy = sy;
-    const unsigned g_rows = persistent_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
+    const unsigned g_rows = fwd_grid(k_fwd<VT, ST, FMT>, h->device, (h->m + h->n) * 32);
     const unsigned g_cols = persistent_grid(adj_kernel<VT, ST, FMT>(h->nz), h->device, (int64_t)h->n * 32);
     const unsigned g_vec = persistent_grid(k_upd<ST>, h->device, h->n);
     const unsigned g_init = persistent_grid(k_init<ST>, h->device, M);
@@ -2071,20 +2184,22 @@ static pdst_status noalloc_run(pdst_handle *h, unsigned char *base, int dtype, b
     PDST_CUDA(cudaMemcpyAsync(sc, &hs, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
     k_init<ST><<<g_init, LT, 0, s>>>(h->m, M, h->n, d, nullptr, ubar, x, wv, partial, sc, sy);
     adj_kernel<VT, ST, FMT>(h->nz)<<<g_cols, LT, 0, s>>>(a, 1);
-    k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
+    k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sc + 1, sy);
     PDST_CUDA(cudaGetLastError());
     launches += 3;
     for (;;) {
         PDST_CUDA(cudaMemcpyAsync(&fin, sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
         PDST_CUDA(cudaStreamSynchronize(s));
         if (fin.done || fin.istop || fin.itn >= fin.itmax) break;
+        // the kernels of Solver::launch_iter, k_step in line (one stream)
         for (int i = 0; i < kblock; ++i) {
+            k_step<<<1, 32, 0, s>>>(sc, sc + 1);
             k_fwd<VT, ST, FMT><<<g_rows, LT, 0, s>>>(a);
+            k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sc + 1, sy);
             adj_kernel<VT, ST, FMT>(h->nz)<<<g_cols, LT, 0, s>>>(a, 0);
-            k_upd<ST><<<g_vec, LT, 0, s>>>(h->n, vbar, x, wv, nullptr, partial, sc, sy);
         }
         PDST_CUDA(cudaGetLastError());
-        launches += 3 * kblock;
+        launches += 4 * kblock;
     }
     k_finalize<<<g_vec, LT, 0, s>>>(h->n, x, a.D, m_out);
     PDST_CUDA(cudaGetLastError());
