@@ -53,7 +53,7 @@ MODEL_PATH = os.path.join(ROOT, "paper_2604_11920_b300", "precond_mlp.json")
 DEFAULT_FORM = "f32-blocked-learned" if os.path.exists(MODEL_PATH) else "f32-blocked-colnorm"
 ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
 TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10)
-REFINE_DTYPE = "df64"                 # refinement sweeps of the reduced-precision forms
+REFINE_DTYPE = "f32"                  # refinement sweeps of the reduced-precision forms
 REF_TOL = 1e-12                       # FP64 reference solve (stops earlier on S4-S6 if need be)
 VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "df64": 8}
 VEC_BYTES = {"f64": 8, "f32": 4, "bf16": 4, "df64": 8}
@@ -258,7 +258,7 @@ def run_pdst(args, rank, world):
 
     p = make_problem(args.workload, rank)
     dtype, fmt, precond = FORMS[args.form]
-    dtypes = sorted({"f64", "df64", dtype})   # df64: the refinement sweeps
+    dtypes = sorted({"f64", "df64", "f32", dtype})   # f32, df64: the refinement sweeps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = pdst.build_G_problem(p, dtypes=tuple(dtypes))
@@ -337,9 +337,10 @@ def run_pdst(args, rank, world):
     # tolerance of the ladder that gets there.  Reduced-precision forms: one
     # solve stalls near the FP32 accuracy limit (large-residual problem), so
     # they run two-phase: the form's solve to tol, then refinement sweeps on the
-    # FP64 residual in double-float arithmetic (FP64 values as float pairs) with
-    # the loosest tolerance of the ladder that gets there.
-    def to_accuracy(form):
+    # FP64 residual (FP32 values; each sweep starts from the exact residual, so
+    # the FP32 operator only slows the contraction) with the loosest tolerance
+    # of the ladder that gets there; double-float sweeps reported beside.
+    def to_accuracy(form, refine_dtype=REFINE_DTYPE):
         dt, fm, pc = FORMS[form]
         err = None
         for t in TOL_LADDER:
@@ -352,14 +353,14 @@ def run_pdst(args, rank, world):
             else:
                 set_scaling(pc)
                 r = h.lsqr(d, p.w, p.lam, 100000, p.tol, dtype=dt, fmt=fm,
-                           precond=1 if pc else 0, refine=3, refine_dtype=REFINE_DTYPE,
+                           precond=1 if pc else 0, refine=3, refine_dtype=refine_dtype,
                            refine_tol=t)
             e1.record(stream)
             torch.cuda.synchronize()
             err = relerr(r.m)
             if err <= ACC_TARGET:
                 if dt != "f64":
-                    return {"refine_tol": t, "refine_dtype": REFINE_DTYPE,
+                    return {"refine_tol": t, "refine_dtype": refine_dtype,
                             "s": e0.elapsed_time(e1) / 1e3, "iters": r.info["iters"],
                             "sweeps": r.info["sweeps"], "model_error": err}
                 return {"tol": t,
@@ -383,6 +384,11 @@ def run_pdst(args, rank, world):
             accuracy_matched["f32-blocked-colnorm"] = acc_cn
             if acc_plain["s"] and acc_cn["s"]:
                 accuracy_matched["speedup_colnorm"] = acc_plain["s"] / acc_cn["s"]
+        # the same two-phase solve with double-float refinement sweeps
+        acc_df = to_accuracy(args.form, "df64")
+        accuracy_matched["df64_refinement"] = acc_df
+        if acc_plain["s"] and acc_df["s"]:
+            accuracy_matched["speedup_df64_refinement"] = acc_plain["s"] / acc_df["s"]
 
     # LSMR (the paper's solver) on the same sweeps: chosen form and plain FP64
     lsmr_sec = None

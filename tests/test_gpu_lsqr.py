@@ -282,6 +282,28 @@ def test_converged_df64_matches_oracle(tiny):
     assert rel(res.m.cpu().numpy(), f64.m.cpu().numpy()) <= 1e-6
 
 
+@pytest.mark.parametrize("precond", [0, 1])
+def test_two_phase_with_fp32_refinement(tiny, precond):
+    """FP32 solve, then refinement sweeps with FP32 values on the FP64 residual:
+    each sweep starts from the exact residual, so the FP32 operator only slows
+    the contraction and the result meets the FP64 minimiser to the parity bar."""
+    p, G, GT, d, h, ref = tiny
+    if precond:
+        h.set_col_scaling(None, p.w, p.lam)
+    one = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype="f32", fmt="blocked", precond=precond)
+    res = h.lsqr(to_dev(d), p.w, p.lam, 20000, 1e-6, dtype="f32", fmt="blocked", precond=precond,
+                 refine=6, refine_dtype="f32", refine_tol=1e-10)
+    e1 = rel(one.m.cpu().numpy(), ref.x)
+    e = rel(res.m.cpu().numpy(), ref.x)
+    print(f"precond={precond}: one solve {e1:.2e}; FP32 sweeps {e:.2e} "
+          f"({res.info['sweeps']} sweeps, {res.info['iters']} it)")
+    assert res.info["sweeps"] >= 2
+    assert e <= 1e-4 and e < e1
+    r_gpu = residual_norm(p, G, res.m.cpu().numpy(), d, p.lam)
+    r_ref = residual_norm(p, G, ref.x, d, p.lam)
+    assert abs(r_gpu - r_ref) / r_ref <= RESID_TOL
+
+
 @pytest.mark.parametrize("dtype,precond", [("f32", 0), ("f32", 1)])
 def test_two_phase_with_df64_refinement(tiny, dtype, precond):
     """FP32 solve, then double-float refinement sweeps on the FP64 residual:
