@@ -79,15 +79,24 @@ def parse_args():
     ap.add_argument("--no-lsmr", action="store_true", help="skip the LSMR section")
     ap.add_argument("--no-sweep", action="store_true", help="skip the damping-sweep section")
     ap.add_argument("--no-accuracy", action="store_true",
-                    help="skip the accuracy-matched ladder (large systems)")
-    ap.add_argument("--ref-tol", type=float, default=REF_TOL,
-                    help="tolerance of the FP64 reference solve")
+                    help="skip the accuracy-matched ladder (skipped by default on "
+                         "--workload large, whose FP64 ladder takes tens of minutes)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="run the accuracy-matched ladder on --workload large too")
+    ap.add_argument("--ref-tol", type=float, default=None,
+                    help="tolerance of the FP64 reference solve (default 1e-12; 1e-10 "
+                         "on --workload large)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the chosen form only (for profiler runs)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small profiler case: build G in the chosen form only and run 3 "
                          "LSQR iterations with plain launches (no timing)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.workload == "large" and not args.accuracy:
+        args.no_accuracy = True
+    if args.ref_tol is None:
+        args.ref_tol = 1e-10 if args.workload == "large" else REF_TOL
+    return args
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
