@@ -777,6 +777,27 @@ __global__ void __launch_bounds__(32) k_step(const LsqrScalars *sc, LsqrScalars 
     }
 }
 
+// The damping sweep's pending steps, one per value still running, beside the
+// forward: warp w advances values w, w + 8, ... on staging copies (published
+// by k_upd_sweep); beta_{i+1} and alpha_{i+1} come from the shared scalars.
+__global__ void __launch_bounds__(LT) k_step_sweep(const LsqrScalars *base, const LsqrScalars *ls,
+                                                    LsqrScalars *stage, int L) {
+    if (!base->step_pending || (base->done | base->istop)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = warp; l < L; l += (int)(blockDim.x >> 5)) {
+        copy_scalars(stage + l, ls + l, lane, 32);
+        __syncwarp();
+        if (lane == 0) {
+            LsqrScalars *c = stage + l;
+            if (!(c->done | c->istop)) {
+                c->beta = base->beta;
+                lsqr_step(c, base->alpha_next);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // u-bar <- (A v-bar)/alpha - (alpha/beta) u-bar;  beta <- ||u-bar||.  BF16
 // values: three blocks per SM, as in the adjoint.
 template <class VT, class ST, int FMT>
@@ -922,16 +943,33 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
     // the blocked sweep's sums, in cell order
     const double cells = (FMT == FMT_BLK && !skip) ? block_sum_ordered(a.cell_ss, a.n_cells) : 0.0;
     if (a.n_lam > 0) {
-        // damping sweep: one recurrence per damping value, one warp each
+        // damping sweep: the start step here (one warp per damping value); later
+        // steps are left pending for k_step_sweep, beside the next forward
         __shared__ double an_s;
         if (threadIdx.x == 0) {
             if (FMT == FMT_BLK) a.sy->count[4] = 0u;   // adjoint work counter for the next launch
             an_s = skip ? alpha : sqrt(tot + cells);
             if (!isfinite(an_s)) sc->err = sc->done = 1;
             sc->alpha_next = an_s;
+            if (!init && isfinite(an_s)) {
+                // the values' states as the last k_upd_sweep published them: the
+                // sweep stops one adjoint after its last value stopped
+                int running = 0;
+                for (int l = 0; l < a.n_lam; ++l) {
+                    const LsqrScalars *c = a.lam_sc + l;
+                    if (c->err) sc->err = 1;
+                    running += !(c->done | c->istop);
+                }
+                sc->alpha = an_s;
+                sc->itn += 1;
+                if (running) sc->step_pending = 1;
+                else sc->istop = 1;
+            }
         }
-        __syncthreads();
-        if (isfinite(an_s)) sweep_step(sc, a.lam_sc, a.n_lam, an_s, init);
+        if (init) {
+            __syncthreads();
+            if (isfinite(an_s)) sweep_step(sc, a.lam_sc, a.n_lam, an_s, init);
+        }
         return;
     }
     if (threadIdx.x == 0) {
@@ -1063,32 +1101,59 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
 }
 
 // Damping sweep, y-slice l of the grid: x_l += t1 w_l; w_l = v + t2 w_l with
-// damping value l's coefficients; ||w_l||^2 to its recurrence.
+// damping value l's coefficients (from k_step_sweep's copy when a step is
+// pending; the slice's last block publishes it); ||w_l||^2 to its recurrence.
+// Every block then arrives on counters[L]; the last one moves beta_next into
+// the shared scalars (all blocks have read step_pending by then).
 template <class ST>
 __global__ void __launch_bounds__(LT) k_upd_sweep(int32_t n, const ST *__restrict__ vbar, double *X,
-                                                  double *W, double *partial, LsqrScalars *ls,
+                                                  double *W, double *partial, LsqrScalars *base,
+                                                  LsqrScalars *ls, LsqrScalars *stage, int L,
                                                   unsigned *counters) {
     const int l = blockIdx.y;
+    const bool pub = base->step_pending != 0;
     LsqrScalars *sc = ls + l;
-    const int pend = sc->pending;
-    if (!pend) return;
-    const double alpha = sc->alpha;
-    const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-    const double t1 = sc->t1, t2 = sc->t2;
-    double *x = X + (int64_t)l * n, *wv = W + (int64_t)l * n;
-    double ss = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        double w = wv[j], xj = x[j];
-        lsqr_xw((double)vbar[j], ia, t1, t2, pend, xj, w);
-        if (pend != 2) x[j] = xj;
-        wv[j] = w;
-        ss = __fma_rn(w, w, ss);
+    const LsqrScalars *src = pub ? stage + l : sc;
+    const int pend = src->pending;
+    if (pend) {
+        const double alpha = src->alpha;
+        const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+        const double t1 = src->t1, t2 = src->t2;
+        double *x = X + (int64_t)l * n, *wv = W + (int64_t)l * n;
+        double ss = 0.0;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            double w = wv[j], xj = x[j];
+            lsqr_xw((double)vbar[j], ia, t1, t2, pend, xj, w);
+            if (pend != 2) x[j] = xj;
+            wv[j] = w;
+            ss = __fma_rn(w, w, ss);
+        }
+        double tot;
+        if (grid_sum_last(ss, partial + (int64_t)l * MAXBLK, counters + l, tot)) {
+            if (pub) {
+                copy_scalars(sc, stage + l, threadIdx.x, blockDim.x);
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                sc->wnorm2 = tot;
+                sc->pending = 0;
+            }
+        }
+    } else if (pub && blockIdx.x == 0) {
+        copy_scalars(sc, stage + l, threadIdx.x, blockDim.x);   // stopped or broken down
     }
-    double tot;
-    if (grid_sum_last(ss, partial + (int64_t)l * MAXBLK, counters + l, tot) && threadIdx.x == 0) {
-        sc->wnorm2 = tot;
-        sc->pending = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(counters + L, 1u);
+        if (t == gridDim.x * gridDim.y - 1) {
+            counters[L] = 0u;
+            if (pub) {
+                base->beta = base->beta_next;
+                base->step_pending = 0;
+            }
+        }
     }
 }
 
@@ -1165,6 +1230,7 @@ struct LsqrWork {
     DevBuf ubar, vbar, vsc, x, wv, hbar, partial, scal, sync, chunk_part, cell_done, cell_ss;
     DevBuf ones, baug, corr;         // refinement: unit scaling, augmented residual, norms
     DevBuf sw_x, sw_w, sw_sc, sw_part, sw_cnt;   // damping sweep: x, w, scalars per value
+    DevBuf sw_stage;                             // damping sweep: k_step_sweep's copies
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
     std::map<int, cudaGraphExec_t> graphs;   // key: kblock
@@ -1794,14 +1860,15 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
     PDST_TRY(w->sw_w.alloc(sizeof(double) * std::max<int64_t>(L * n, 1)));
     PDST_TRY(w->sw_sc.alloc(sizeof(LsqrScalars) * L));
     PDST_TRY(w->sw_part.alloc(sizeof(double) * L * MAXBLK));
-    PDST_TRY(w->sw_cnt.alloc(sizeof(unsigned) * L));
+    PDST_TRY(w->sw_cnt.alloc(sizeof(unsigned) * (L + 1)));   // per value, + all blocks
+    PDST_TRY(w->sw_stage.alloc(sizeof(LsqrScalars) * L));
     OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, false, false);
     a.lam_sc = w->sw_sc.as<LsqrScalars>();
     a.n_lam = L;
     double *X = w->sw_x.as<double>(), *W = w->sw_w.as<double>();
     PDST_CUDA(cudaMemsetAsync(w->sync.p, 0, sizeof(LsqrSync), s));
     PDST_CUDA(cudaMemsetAsync(w->cell_done.p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
-    PDST_CUDA(cudaMemsetAsync(w->sw_cnt.p, 0, sizeof(unsigned) * L, s));
+    PDST_CUDA(cudaMemsetAsync(w->sw_cnt.p, 0, sizeof(unsigned) * (L + 1), s));
     PDST_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * L * n, s));
     *w->h_scal = base0;
     PDST_CUDA(cudaMemcpyAsync(w->scal.p, w->h_scal, sizeof(LsqrScalars), cudaMemcpyHostToDevice, s));
@@ -1812,8 +1879,9 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
     k_init<ST><<<ginit, LT, 0, s>>>(h->m, w->M, h->n, d, nullptr, a.ubar, a.x, a.wv, a.partial,
                                     a.sc, a.sy);
     adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 1);
-    k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.lam_sc,
-                                      w->sw_cnt.as<unsigned>());
+    LsqrScalars *stage = w->sw_stage.as<LsqrScalars>();
+    k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.sc,
+                                      a.lam_sc, stage, L, w->sw_cnt.as<unsigned>());
     PDST_CUDA(cudaGetLastError());
     launches += 3;
     for (;;) {
@@ -1822,14 +1890,20 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
         PDST_CUDA(cudaStreamSynchronize(s));
         const LsqrScalars &c = *w->h_scal;
         if (c.done || c.istop || c.err || c.itn >= c.itmax) break;
+        // the order of Solver::launch_iter, with the sweep's step and update
         for (int i = 0; i < kblock; ++i) {
+            cudaEventRecord(w->ev_fork, s);
+            cudaStreamWaitEvent(w->side, w->ev_fork, 0);
+            k_step_sweep<<<1, LT, 0, w->side>>>(a.sc, a.lam_sc, stage, L);
+            cudaEventRecord(w->ev_join, w->side);
             k_fwd<VT, ST, FMT><<<w->grid_rows, LT, 0, s>>>(a);
+            cudaStreamWaitEvent(s, w->ev_join, 0);
+            k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.sc,
+                                              a.lam_sc, stage, L, w->sw_cnt.as<unsigned>());
             adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
-            k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(),
-                                              a.lam_sc, w->sw_cnt.as<unsigned>());
         }
         PDST_CUDA(cudaGetLastError());
-        launches += 3 * kblock;
+        launches += 4 * kblock;
     }
     for (int l = 0; l < L; ++l)
         k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, X + (int64_t)l * n, nullptr, m_out[l], 0);
