@@ -1303,13 +1303,17 @@ template <class VT, class ST, int FMT> static auto adj_kernel(int nz) {
     return k_adj<VT, ST, FMT, G_ANY>;
 }
 
-// The forward kernel for a handle: FP32 values with nz = 20 (compile-time
-// quads of 5) run three blocks per SM (up to 85 registers), measured 12 %
-// faster on 100 x 100 x 20; at nz = 16 and 18 three blocks were 2 % and 12 %
-// slower, so the other depth counts keep four.
+// The forward kernel for a handle.  With FP32 values three blocks per SM (up
+// to 85 registers) against four, measured per depth path on B300: run-time
+// quads -7 % (nz = 12) and -18 % (24), compile-time quads of 5 -12 % (20),
+// pairs -6 % (10); but quads of 4 +2 % (16), six-entry groups +12 % (18) and
+// one entry per lane +19 % (15), which keep four (as do quads of 2, nz = 8).
+__host__ __device__ constexpr bool fwd_three_blocks(int nz) {
+    return (nz & 3) == 0 ? (nz != 16 && nz != 8) : ((nz & 1) == 0 && nz % 6 != 0);
+}
 template <class VT, class ST, int FMT> static auto fwd_kernel(int nz) {
     if constexpr (FMT == FMT_BLK && sizeof(VT) == 4 && sizeof(ST) == 4) {
-        if (nz == 20) return k_fwd<VT, ST, FMT, 3>;
+        if (fwd_three_blocks(nz)) return k_fwd<VT, ST, FMT, 3>;
     }
     return k_fwd<VT, ST, FMT>;
 }
