@@ -237,11 +237,15 @@ pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lam
  * one file-scope device array of 16 MiB that every GPU which loads the
  * library holds until the process exits.
  *
- * Arguments and results are those of pdst_lsqr (same kernels, same answer);
- * the iterations are plain kernel launches (opts->use_graph is ignored) and
- * opts->profile must be 0.  The handle's device must be the current device.
- * The first call on a device looks up the array's device address there
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Arguments and results are those of pdst_lsqr (same kernels in the same
+ * order, same answer bit for bit); the iterations are plain kernel launches
+ * (opts->use_graph is ignored), opts->profile and opts->refine must be 0 and
+ * opts->method PDST_LSQR (PDST_ERR_ARG otherwise).  The handle's device must
+ * be the current device.  The first call on a device looks up the array's
+ * device address there (cudaGetSymbolAddress) and keeps it for later calls;
+ * make that first call before any stream capture, and do not call this
+ * function again on a device after cudaDeviceReset there (the module, and
+ * with it the array, may then live at another address).
  * Every call on a device shares the one array, which keeps the previous
  * call's contents (the function clears what must start at zero): calls that
  * overlap on the GPU -- from two host threads or on two streams -- race and

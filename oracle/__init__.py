@@ -78,7 +78,7 @@ def _load():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     _d, ctypes.c_double, ctypes.c_double, _d, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _d, _d,
-                                    ctypes.c_int, _d, _d, _d]
+                                    ctypes.c_int, _d, _d, _d, ctypes.c_int, _d, _d, _i32]
         lib.oracle_lsqr.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -230,13 +230,18 @@ class LSQRResult:
     U: Optional[np.ndarray] = None
     V: Optional[np.ndarray] = None
     rhist: Optional[np.ndarray] = None
+    ck_itn: Optional[np.ndarray] = None   # per checkpoint tolerance: stopping iteration (0: never)
+    ck_x: Optional[np.ndarray] = None     # per checkpoint tolerance: the iterate there
 
 
 def lsqr(G: CSR, GT: CSR, grid, w: float, damp: float, b: np.ndarray,
          atol: float = 1e-8, btol: float = 1e-8, conlim: float = 1e8, itmax: int = 300,
          D: Optional[np.ndarray] = None, lam_rows: float = 0.0, record: int = 0,
-         history: bool = False) -> LSQRResult:
-    """LSQR on [G; w L] (or [G D; w L D; lam_rows D] when D is given)."""
+         history: bool = False, checkpoints=None) -> LSQRResult:
+    """LSQR on [G; w L] (or [G D; w L D; lam_rows D] when D is given).
+
+    checkpoints: tolerances t; for each, the iterate and iteration at which a
+    solve with atol = btol = t stops on S1 or S2 (the same run serves all)."""
     lib = _load()
     nx, ny, nz = grid
     m, n = G.n_rows, G.n_cols
@@ -249,17 +254,23 @@ def lsqr(G: CSR, GT: CSR, grid, w: float, damp: float, b: np.ndarray,
     U = np.zeros((record, M)) if record > 0 else None
     V = np.zeros((record, n)) if record > 0 else None
     rh = np.zeros(max(itmax, 1)) if history else None
+    ck = None if checkpoints is None else np.ascontiguousarray(checkpoints, dtype=np.float64)
+    nck = 0 if ck is None else int(ck.shape[0])
+    ck_x = np.zeros((nck, n)) if nck else None
+    ck_itn = np.zeros(nck, dtype=np.int32) if nck else None
     rc = lib.oracle_lsqr(m, n, _p(G.ptr, _i64), _p(G.idx, _i32), _p(G.val, _d),
                          _p(GT.ptr, _i64), _p(GT.idx, _i32), _p(GT.val, _d),
                          nx, ny, nz, w, _p(D, _d), lam_rows, damp, _p(b, _d),
                          atol, btol, conlim, itmax, _p(x, _d), _p(est, _d),
-                         record, _p(U, _d), _p(V, _d), _p(rh, _d))
+                         record, _p(U, _d), _p(V, _d), _p(rh, _d),
+                         nck, _p(ck, _d), _p(ck_x, _d), _p(ck_itn, _i32))
     if rc != 0:
         raise MemoryError("oracle_lsqr")
     itn = int(est[0])
     return LSQRResult(x=x, itn=itn, istop=int(est[1]), rnorm=est[2], arnorm=est[3],
                       anorm=est[4], acond=est[5], xnorm=est[6], bnorm=est[7],
-                      U=U, V=V, rhist=None if rh is None else rh[:itn])
+                      U=U, V=V, rhist=None if rh is None else rh[:itn],
+                      ck_itn=ck_itn, ck_x=ck_x)
 
 
 def rhs_for(p, G: CSR, m_model=None, noise=None, frac=None) -> np.ndarray:

@@ -428,7 +428,8 @@ int oracle_lsqr(int64_t m, int32_t n, const int64_t *rp, const int32_t *ci,
                 int nx, int ny, int nz, double w, const double *D, double lam_rows,
                 double damp, const double *b, double atol, double btol, double conlim,
                 int itmax, double *x, double *est, int rec_k, double *U, double *V,
-                double *rhist)
+                double *rhist, int n_ck, const double *ck_tol, double *ck_x,
+                int32_t *ck_itn)
 {
     op_t A = {m, n, rp, ci, va, cp, ri, vt, nx, ny, nz, w, D, lam_rows, NULL, NULL};
     int64_t M = op_rows(&A);
@@ -549,6 +550,18 @@ int oracle_lsqr(int64_t m, int32_t n, const int64_t *rp, const int32_t *ci,
             double test3 = 1.0 / (acond + eps);
             double t1s = test1 / (1.0 + anorm * xnorm / bnorm);
             double rtol = btol + atol * anorm * xnorm / bnorm;
+            /* checkpoints (output only): the iterate at which a solve with
+             * atol = btol = ck_tol[c] would stop on S1 or S2 -- the iteration
+             * does not depend on the tolerances, so that solve's answer */
+            for (int c = 0; c < n_ck; ++c) {
+                if (ck_itn[c] > 0)
+                    continue;
+                double tc = ck_tol[c];
+                if (test1 <= tc + tc * anorm * xnorm / bnorm || test2 <= tc) {
+                    ck_itn[c] = itn;
+                    memcpy(ck_x + (size_t)c * n, x, sizeof(double) * (size_t)n);
+                }
+            }
             if (test1 <= rtol) istop = 1;
             else if (test2 <= atol) istop = 2;
             else if (test3 <= ctol) istop = 3;

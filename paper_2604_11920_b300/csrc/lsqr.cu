@@ -2323,6 +2323,9 @@ extern "C" pdst_status pdst_lsqr_noalloc(pdst_handle_t h, const double *d_dev, d
     PDST_CHECK_ARG(h->m == 0 || d_dev, "pdst_lsqr_noalloc: d is NULL");
     PDST_CHECK_ARG(m_out_dev, "pdst_lsqr_noalloc: m_out is NULL");
     PDST_CHECK_ARG(opts.profile == 0, "pdst_lsqr_noalloc: profile mode is not available");
+    PDST_CHECK_ARG(opts.refine == 0,
+                   "pdst_lsqr_noalloc: refinement sweeps are not available (refine %d)",
+                   opts.refine);
     PDST_CHECK_ARG(opts.precond == 0 || opts.precond == 1,
                    "pdst_lsqr_noalloc: unknown precond %d", opts.precond);
     if (!h->vals[dtype].present) {

@@ -106,3 +106,78 @@ def test_bad_arguments():
     d = torch.zeros((h.m, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
         pdst.lsqr_batched([h], [d], [1.0], [[0.1, 0.2]], 10, 1e-6, dtype="f64")
+
+
+# ------------------------------------------ the 16-right-hand-side fast paths
+# With 9-16 right-hand sides (RS = 16) and nz = 8 or 16 the batched forward and
+# adjoint run compile-time paths (two runs in flight; 4 x 4 outer products per
+# lane), the ones the 64-system workload runs.  Each column is checked against
+# the FP64 oracle directly: element by element at a fixed iteration count
+# (FP64 values), and converged columns against the oracle's tol-1e-12
+# solution (FP64 within 1e-4; FP32 within what the oracle itself reaches at
+# the same tolerance, plus 1e-3).
+
+def nzc_batch():
+    probs = [synth.custom(14, 12, 8, 16, 5, bend=0.15, seed=51, w=1.0, lam=0.1),
+             synth.custom(11, 13, 16, 15, 6, bend=0.15, seed=52, w=2.0, lam=0.05, dz_km=1.0),
+             synth.custom(10, 9, 16, 12, 4, bend=0.1, seed=53, w=1.0, lam=0.1, dz_km=1.0)]
+    nrhs = [16, 16, 13]
+    out = []
+    for p, R in zip(probs, nrhs):
+        G = oracle.build_G_problem(p)
+        cols, lams = [], []
+        for j in range(R):
+            m = synth.checkerboard(p.nx, p.ny, p.nz, 2 + (j % 7), 0.05) * (1 if j % 2 else -1)
+            cols.append(oracle.rhs_for(p, G, m_model=m, noise=synth.rhs_noise(p.seed, p.m_rows, j)))
+            lams.append(float(np.logspace(-3, 0, R)[j]))
+        out.append((p, G, oracle.transpose(G), np.stack(cols, axis=1), lams))
+    return out
+
+
+@pytest.fixture(scope="module")
+def nzc():
+    require_cuda()
+    b = nzc_batch()
+    hs = [pdst.build_G_problem(p, dtypes=("f64", "f32"), formats=("blocked",))
+          for p, _, _, _, _ in b]
+    yield b, hs
+    for h in hs:
+        h.close()
+
+
+@pytest.mark.parametrize("k", [1, 4, 8])
+def test_nzc_paths_fixed_k_match_oracle(nzc, k):
+    b, hs = nzc
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, *_ in b], [l for *_, l in b], k, 0.0,
+                                       dtype="f64", tile_rows=2)
+    for (p, G, GT, D, lams), mo, inf in zip(b, outs, infos):
+        got = mo.cpu().numpy()
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, lams[j], D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k)
+            assert inf[j]["iters"] == k
+            assert rel(got[:, j], ref.x) < 1e-10, (p.nz, j, k)
+            for key in ("rnorm", "arnorm", "anorm", "xnorm"):
+                assert abs(inf[j][key] - getattr(ref, key)) <= 1e-10 * abs(getattr(ref, key)), key
+
+
+def test_nzc_paths_converged_match_oracle(nzc):
+    b, hs = nzc
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    w = [p.w for p, *_ in b]
+    lams = [l for *_, l in b]
+    o64, i64, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-10, dtype="f64")
+    o32, i32, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32")
+    for (p, G, GT, D, lj), m64, m32, inf64, inf32 in zip(b, o64, o32, i64, i32):
+        for j in range(D.shape[1]):
+            grid = (p.nx, p.ny, p.nz)
+            ref = oracle.lsqr(G, GT, grid, p.w, lj[j], D[:, j], atol=1e-12, btol=1e-12,
+                              itmax=50000)
+            same = oracle.lsqr(G, GT, grid, p.w, lj[j], D[:, j], atol=1e-6, btol=1e-6,
+                               itmax=50000)
+            assert inf64[j]["istop"] in (1, 2) and inf32[j]["istop"] in (1, 2)
+            assert rel(m64[:, j].cpu().numpy(), ref.x) <= 1e-4, (p.nz, j)
+            e32 = rel(m32[:, j].cpu().numpy(), ref.x)
+            e_or = rel(same.x, ref.x)
+            assert e32 <= 2.0 * e_or + 1e-3, (p.nz, j, e32, e_or)

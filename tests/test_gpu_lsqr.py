@@ -339,13 +339,15 @@ def test_df64_form_errors(tiny):
     h2.close()
 
 
-# ------------------------------------------------ depth counts off the quad paths
-# nz % 4 == 0 uses 4-entry vector loads (compile-time for 8, 16, 20, run-time
-# otherwise, e.g. 12); nz % 6 == 0 otherwise 6-entry groups in the forward and
-# three pairs per lane in the adjoint (6, 18, 30: the paper's 18 depth nodes);
-# other even nz 2-entry pairs (10, 14); odd nz one entry per lane (5).
+# ------------------------------------------------ every depth-count path
+# nz % 4 == 0 uses 4-entry vector loads (compile-time quads for 8, 16 and 20 --
+# the paths of the 64 x 64 x 16 and 100 x 100 x 20 workloads -- run-time
+# quads otherwise, e.g. 12); nz % 6 == 0 otherwise 6-entry groups in the
+# forward and three pairs per lane in the adjoint (6, 18, 30: the paper's 18
+# depth nodes); other even nz 2-entry pairs (10, 14); odd nz one entry per
+# lane (5).
 
-@pytest.mark.parametrize("nz", [5, 6, 10, 12, 14, 18, 30])
+@pytest.mark.parametrize("nz", [5, 6, 8, 10, 12, 14, 16, 18, 20, 30])
 def test_fixed_k_iterates_other_depth_counts(nz):
     require_cuda()
     p = synth.make_problem(f"nz{nz}", 12, 10, nz, 14, np.geomspace(2.0, 16.0, 5), bend=0.15,

@@ -203,3 +203,20 @@ def test_zero_rhs_and_zero_iterations(tiny_system):
     assert r0.itn == 0 and r0.istop == 0 and not r0.x.any()
     r1 = oracle.lsqr(G, GT, grid, p.w, p.lam, d, itmax=0)
     assert r1.itn == 0 and not r1.x.any()
+
+
+def test_checkpoints_equal_separate_solves(tiny_system):
+    """The checkpoint output of one run is, for each tolerance t, exactly what a
+    separate solve with atol = btol = t returns (the iteration does not depend
+    on the tolerances; only the stopping point does)."""
+    p, G, GT, d = tiny_system
+    grid = (p.nx, p.ny, p.nz)
+    ladder = (1e-3, 1e-5, 1e-7, 1e-9)
+    one = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=1e-12, btol=1e-12, itmax=20000,
+                      checkpoints=ladder)
+    assert np.all(np.diff(one.ck_itn) >= 0) and one.ck_itn[0] > 0
+    for c, t in enumerate(ladder):
+        sep = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=t, btol=t, itmax=20000)
+        assert sep.istop in (1, 2)
+        assert one.ck_itn[c] == sep.itn
+        assert np.array_equal(one.ck_x[c], sep.x)

@@ -1,4 +1,4 @@
-"""pdst_lsqr_noalloc, the allocation-free solve, against pdst_lsqr.
+"""pdst_lsqr_noalloc, the allocation-free solve, against pdst_lsqr and the oracle.
 
 Callers that must not allocate device memory while they run (a serving or
 plugin host that owns all device memory, a process under a hard memory cap,
@@ -6,8 +6,11 @@ a loop that cannot take cudaFree's device-wide synchronisation) use this entry
 point: its scratch is one static device array in the library.  The test calls
 it through the C ABI twice in a row -- the array keeps the previous call's
 contents, so the second call checks that nothing stale leaks in -- and
-compares each result with pdst_lsqr's within the tolerance of the fixed-k
-parity tests.  This file is collected last on purpose.
+compares each result with pdst_lsqr's: the same kernels run in the same
+order, so the models and the reported fields agree bit for bit.  One more
+case runs the column-scaled operator with lambda rows appended (which moves
+every later carve of the array), and one compares a fixed-k run with the FP64
+oracle directly.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -18,7 +21,13 @@ from gpu_util import rel, require_cuda, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10
+FIELDS = ("iters", "istop", "rnorm", "arnorm", "anorm", "acond", "xnorm", "bnorm")
+
+
+def _same(got, ref):
+    assert np.array_equal(got.m.cpu().numpy(), ref.m.cpu().numpy())
+    for key in FIELDS:
+        assert got.info[key] == ref.info[key], key
 
 
 def test_noalloc_matches_lsqr_on_two_calls_in_a_row():
@@ -33,11 +42,37 @@ def test_noalloc_matches_lsqr_on_two_calls_in_a_row():
         ref = h.lsqr(dd, p.w, p.lam, itmax, tol, **form)
         out = torch.full((h.n,), float("nan"), dtype=torch.float64, device="cuda")
         got = h.lsqr_noalloc(dd, p.w, p.lam, itmax, tol, out, **form)
-        assert got.info["iters"] == ref.info["iters"] > 0
-        assert got.info["istop"] == ref.info["istop"]
-        assert rel(got.m.cpu().numpy(), ref.m.cpu().numpy()) <= TOL
-        for key in ("rnorm", "arnorm", "anorm", "xnorm"):
-            assert abs(got.info[key] - ref.info[key]) <= TOL * abs(ref.info[key])
+        assert got.info["iters"] > 0
+        _same(got, ref)
+    h.close()
+
+
+def test_noalloc_scaled_with_lambda_rows_and_oracle():
+    """precond = 1 with lambda > 0 appends the lambda D rows (M = m + 2n):
+    equal to pdst_lsqr bit for bit, and at a fixed iteration count equal to
+    the oracle's scaled LSQR within the FP64 fixed-k bar."""
+    torch = require_cuda()
+    p = synth.tiny()
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    h = pdst.build_G_problem(p, dtypes=("f64",))
+    D = 1.0 / np.sqrt(oracle.aug_colnorm2(GT, p.nx, p.ny, p.nz, p.w, p.lam))
+    h.set_col_scaling(to_dev(D))
+    dd = to_dev(d)
+    for fmt in ("element", "blocked"):
+        ref = h.lsqr(dd, p.w, p.lam, 500, 1e-8, fmt=fmt, precond=1)
+        out = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+        _same(h.lsqr_noalloc(dd, p.w, p.lam, 500, 1e-8, out, fmt=fmt, precond=1), ref)
+    k = 6
+    o = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, d, atol=0, btol=0, conlim=0, itmax=k,
+                    D=D, lam_rows=p.lam)
+    out = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    got = h.lsqr_noalloc(dd, p.w, p.lam, k, 0.0, out, fmt="blocked", precond=1, conlim=1e300)
+    assert got.info["iters"] == k
+    assert rel(got.m.cpu().numpy(), D * o.x) < 1e-10
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_ARG"):
+        h.lsqr_noalloc(dd, p.w, p.lam, 10, 1e-6, out, refine=2)
     h.close()
 
 
