@@ -87,7 +87,10 @@ typedef struct {
                               each chord's length split over the four grid nodes around its
                               midpoint (nodes at cell centres, so the columns keep the cell
                               numbering; needs nx, ny >= 2) */
-    int32_t reserved0;
+    int32_t keep_lengths;  /* 1: keep each (row, cell) run's ray length and its place in the
+                              transposed layout, so that pdst_set_depth_kernels can replace
+                              the depth kernels later (20 bytes per run); 0 (default): free
+                              them after assembly */
 } pdst_build_opts;
 
 /*
@@ -392,6 +395,84 @@ pdst_status pdst_mlp_grad(const float *params_dev, const float *feat_dev, const 
 pdst_status pdst_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
                           int64_t step, double lr, double beta1, double beta2, double eps,
                           void *stream);
+
+/* ---- outer nonlinear loop ------------------------------------------------
+ * The paper's inversion (after Eq. 6) solves Eq. 6 for the model
+ * perturbation, updates the model, rebuilds G from the updated model and
+ * repeats until the RMS traveltime error falls below a threshold.  The rays
+ * (the traveltime module) stay fixed here; what follows the model is the depth
+ * kernel of each horizontal cell, by this synthetic kernel module: with
+ * s_h = (1/nz) sum_k (1 + m[h*nz + k]) (the column's mean relative S-wave
+ * velocity, summed in depth order) and a = kernel_power,
+ *     z0(h, t) = z0_factor * T_t * s_h^a,
+ *     K[h][t][k] = (z_k / z0) * exp(1 - z_k / z0) * dz,  z_k = (k + 1/2) dz,
+ * a faster column being sampled deeper (the 1-D table of Eq. 5's synthetic
+ * form at m = 0). */
+
+/* K (device, nx*ny x n_periods x nz FP64, cell slowest, depth fastest) from
+ * the model m_dev (n FP64, device); periods_host: n_periods values T (host).
+ * The grid's dz_km is the layer thickness.  Asynchronous on `stream`.
+ * Errors: PDST_ERR_ARG (NULL pointers, non-finite or non-positive factor or
+ * period). */
+pdst_status pdst_depth_kernels_from_model(pdst_handle_t h, const double *periods_host,
+                                          double z0_factor, double kernel_power,
+                                          const double *m_dev, double *kdz_cells_dev,
+                                          void *stream);
+
+/* Replace the depth kernels of G: every kept value copy (all dtypes and
+ * layouts) is expanded again as value(r, h, k) = l_h(r) * K[h][t(r)][k] from
+ * the per-cell table kdz_cells_dev (device, as above), the ray lengths and the
+ * sparsity pattern unchanged -- the same values pdst_build_G gives with that
+ * table as kdz_cells.  A scaling set by pdst_set_col_scaling is not updated.
+ * Needs keep_lengths at assembly (PDST_ERR_STATE otherwise).  Synchronous. */
+pdst_status pdst_set_depth_kernels(pdst_handle_t h, const double *kdz_cells_dev, void *stream);
+
+typedef struct {
+    int32_t max_outer;     /* model updates at most (default 8) */
+    int32_t reserved0;
+    double rms_tol;        /* stop once RMS <= rms_tol (default 0) */
+    double min_decrease;   /* stop once the RMS fell by less than this fraction since the
+                              previous model (default 0.01); if it rose, the previous model
+                              is returned */
+    double z0_factor;      /* kernel depth per period (default 1.2 km/s) */
+    double kernel_power;   /* a above (default 1; 0: the kernels do not follow the model) */
+    pdst_lsqr_opts inner;  /* options of each update's solve (pdst_lsqr); with precond = 1
+                              the column-norm scaling of the current G is set before each
+                              solve */
+} pdst_outer_opts;
+
+/* Fill *o with the defaults listed above (inner: pdst_lsqr_opts_default). */
+void pdst_outer_opts_default(pdst_outer_opts *o);
+
+typedef struct {
+    int32_t updates;       /* model updates made */
+    int32_t reason;        /* 1 RMS <= rms_tol; 2 the RMS stopped decreasing; 3 max_outer */
+    int32_t inner_iters;   /* LSQR iterations over all updates */
+    int32_t reserved;
+    double rms_first;      /* RMS of d_obs - G(0) 0 = d_obs */
+    double rms_final;      /* RMS of the returned model */
+} pdst_outer_info;
+
+/*
+ * The outer loop from m = 0: for the current model m, K = kernels(m)
+ * (pdst_depth_kernels_from_model), G(m) (pdst_set_depth_kernels), the data
+ * residual r = d_obs - G(m) m and RMS = sqrt(mean(r^2)) (FP64 values); stop as
+ * opts says (checked before each solve); else solve Eq. 6 for the update
+ *     dm = argmin ||G(m) dm - r||^2 + w^2 ||L dm||^2 + lambda^2 ||dm||^2
+ * by pdst_lsqr (itmax, tol, opts->inner) and set m <- m + dm.
+ *   d_obs_dev     m_rows FP64 observed traveltime perturbations (device)
+ *   periods_host  n_periods values T of the handle's periods (host)
+ *   m_out_dev     n FP64 (device): the final model
+ *   rms_hist_host NULL or max_outer + 1 doubles: the RMS before each solve and of
+ *                 the final model (updates + 1 entries written)
+ * The handle needs FP64 values and keep_lengths; its values end as G of the
+ * last model checked.  Synchronous.  Errors: as pdst_lsqr and
+ * pdst_set_depth_kernels.
+ */
+pdst_status pdst_outer_loop(pdst_handle_t h, const double *d_obs_dev, const double *periods_host,
+                            double w, double lambda, int32_t itmax, double tol,
+                            const pdst_outer_opts *opts, double *m_out_dev,
+                            double *rms_hist_host, pdst_outer_info *info, void *stream);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdst_last_error_string(void);

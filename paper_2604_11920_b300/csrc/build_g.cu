@@ -487,9 +487,55 @@ static unsigned grid_for(int64_t work, int threads, int device) {
     return (unsigned)b;
 }
 
+// Blocked-CSC copies of every kept value set (and element-CSC copies with the
+// element layout) from its CSR-order values; rp = each run's position in the
+// blocked CSC layout.  Asynchronous.
+static pdst_status transposed_value_copies(pdst_handle *h, const int64_t *rp, cudaStream_t s) {
+    const int64_t U = h->U, nnz = h->nnz;
+    const int nz = h->nz;
+    if (!nnz) return PDST_OK;
+    unsigned g = grid_for(nnz, 256, h->device);
+    const bool elem = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
+    if (h->vals[0].present) {
+        k_bcsc_values<double><<<g, 256, 0, s>>>(U, nz, rp, h->vals[0].csr.as<double>(),
+                                               h->vals[0].bcsc.as<double>());
+        if (elem)
+            k_csc_values<double><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
+                                                  h->cell_rptr.as<int64_t>(),
+                                                  h->cell_cnt.as<int32_t>(),
+                                                  h->vals[0].csr.as<double>(),
+                                                  h->vals[0].csc.as<double>());
+    }
+    if (h->vals[1].present) {
+        k_bcsc_values<float><<<g, 256, 0, s>>>(U, nz, rp, h->vals[1].csr.as<float>(),
+                                              h->vals[1].bcsc.as<float>());
+        if (elem)
+            k_csc_values<float><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
+                                                 h->cell_rptr.as<int64_t>(),
+                                                 h->cell_cnt.as<int32_t>(),
+                                                 h->vals[1].csr.as<float>(),
+                                                 h->vals[1].csc.as<float>());
+    }
+    if (h->vals[PDST_DF64].present)
+        k_bcsc_values<dfl><<<g, 256, 0, s>>>(U, nz, rp, h->vals[PDST_DF64].csr.as<dfl>(),
+                                            h->vals[PDST_DF64].bcsc.as<dfl>());
+    if (h->vals[2].present) {
+        k_bcsc_values<__nv_bfloat16><<<g, 256, 0, s>>>(U, nz, rp,
+                                                      h->vals[2].csr.as<__nv_bfloat16>(),
+                                                      h->vals[2].bcsc.as<__nv_bfloat16>());
+        if (elem)
+            k_csc_values<__nv_bfloat16><<<g, 256, 0, s>>>(
+                U, nz, h->row_cells.as<int32_t>(), rp, h->cell_rptr.as<int64_t>(),
+                h->cell_cnt.as<int32_t>(), h->vals[2].csr.as<__nv_bfloat16>(),
+                h->vals[2].csc.as<__nv_bfloat16>());
+    }
+    PDST_CUDA(cudaGetLastError());
+    return PDST_OK;
+}
+
 static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int32_t *per_host,
                               const double *kdz_host, const double *kdz_cells_host,
-                              uint32_t dtypes, cudaStream_t s) {
+                              uint32_t dtypes, bool keep_lengths, cudaStream_t s) {
     const int nx = h->grid.nx, ny = h->grid.ny, nz = h->nz, H = h->H;
     const double dx = h->grid.dx_km;
     const int64_t m = h->m;
@@ -639,42 +685,7 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
                                                        h->cell_rows.as<int32_t>(),
                                                        d_runpos.as<int64_t>());
         PDST_CUDA(cudaGetLastError());
-        unsigned g = grid_for(nnz, 256, h->device);
-        const bool elem = (h->formats & (1u << PDST_FMT_ELEMENT)) != 0;
-        const int64_t *rp = d_runpos.as<int64_t>();
-        if (h->vals[0].present) {
-            k_bcsc_values<double><<<g, 256, 0, s>>>(U, nz, rp, h->vals[0].csr.as<double>(),
-                                                   h->vals[0].bcsc.as<double>());
-            if (elem)
-                k_csc_values<double><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
-                                                      h->cell_rptr.as<int64_t>(),
-                                                      h->cell_cnt.as<int32_t>(),
-                                                      h->vals[0].csr.as<double>(),
-                                                      h->vals[0].csc.as<double>());
-        }
-        if (h->vals[1].present) {
-            k_bcsc_values<float><<<g, 256, 0, s>>>(U, nz, rp, h->vals[1].csr.as<float>(),
-                                                  h->vals[1].bcsc.as<float>());
-            if (elem)
-                k_csc_values<float><<<g, 256, 0, s>>>(U, nz, h->row_cells.as<int32_t>(), rp,
-                                                     h->cell_rptr.as<int64_t>(),
-                                                     h->cell_cnt.as<int32_t>(),
-                                                     h->vals[1].csr.as<float>(),
-                                                     h->vals[1].csc.as<float>());
-        }
-        if (h->vals[PDST_DF64].present)
-            k_bcsc_values<dfl><<<g, 256, 0, s>>>(U, nz, rp, h->vals[PDST_DF64].csr.as<dfl>(),
-                                                h->vals[PDST_DF64].bcsc.as<dfl>());
-        if (h->vals[2].present) {
-            k_bcsc_values<__nv_bfloat16><<<g, 256, 0, s>>>(U, nz, rp,
-                                                          h->vals[2].csr.as<__nv_bfloat16>(),
-                                                          h->vals[2].bcsc.as<__nv_bfloat16>());
-            if (elem)
-                k_csc_values<__nv_bfloat16><<<g, 256, 0, s>>>(
-                    U, nz, h->row_cells.as<int32_t>(), rp, h->cell_rptr.as<int64_t>(),
-                    h->cell_cnt.as<int32_t>(), h->vals[2].csr.as<__nv_bfloat16>(),
-                    h->vals[2].csc.as<__nv_bfloat16>());
-        }
+        PDST_TRY(transposed_value_copies(h, d_runpos.as<int64_t>(), s));
         PDST_CUDA(cudaGetLastError());
         PDST_CUDA(cudaStreamSynchronize(s));   // chunk tables are released on scope exit
     }
@@ -728,6 +739,12 @@ static pdst_status build_impl(pdst_handle *h, const double *ctrl_host, const int
         PDST_TRY(h->adj_item.alloc(sizeof(int32_t) * items.size()));
         PDST_CUDA(cudaMemcpy(h->adj_item.p, items.data(), sizeof(int32_t) * items.size(),
                              cudaMemcpyHostToDevice));
+    }
+    if (keep_lengths) {
+        h->run_len.take(d_lens);
+        h->run_row.take(d_runrow);
+        h->run_pos.take(d_runpos);
+        h->has_lengths = true;
     }
     return PDST_OK;
 }
@@ -790,11 +807,109 @@ extern "C" pdst_status pdst_build_G(const pdst_grid *grid, int64_t n_paths,
     h->formats = formats;
     h->interp = interp;
     pdst_status st = build_impl(h, ctrl_host, path_period_host, kdz_host, kdz_cells, dtypes,
-                                (cudaStream_t)stream);
+                                opts && opts->keep_lengths, (cudaStream_t)stream);
     if (st != PDST_OK) {
         delete h;
         return st;
     }
     *out = h;
+    return PDST_OK;
+}
+
+// ------------------------------------------------ depth kernels from a model
+//
+// The synthetic kernel module of the outer loop (the paragraph after Eq. 6:
+// G is rebuilt from the updated model): under cell h the kernel depth follows
+// the column's mean relative velocity s_h = (1/nz) sum_k (1 + m[h*nz + k]),
+// z0 = z0_factor * T * s_h^a, K[h][t][k] = (z_k / z0) exp(1 - z_k / z0) dz.
+// One rounding per written operation (this file has no FMA contraction).
+
+namespace pdst {
+
+__global__ void k_kernels_from_model(int32_t H, int nz, int T, const double *__restrict__ periods,
+                                     double z0f, double kp, double dz,
+                                     const double *__restrict__ mv, double *__restrict__ K) {
+    const int64_t total = (int64_t)H * T;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = i / T;
+        const int t = (int)(i - h * T);
+        const double *col = mv + h * nz;
+        double s = 0.0;
+        for (int k = 0; k < nz; ++k) s = s + (1.0 + col[k]);   // depth order
+        s = s / (double)nz;
+        if (kp != 1.0) s = pow(s, kp);
+        const double z0 = (z0f * periods[t]) * s;
+        double *out = K + i * nz;
+        for (int k = 0; k < nz; ++k) {
+            const double z = ((double)k + 0.5) * dz;
+            const double q = z / z0;
+            out[k] = (q * exp(1.0 - q)) * dz;
+        }
+    }
+}
+
+}  // namespace pdst
+
+extern "C" pdst_status pdst_depth_kernels_from_model(pdst_handle_t h, const double *periods_host,
+                                                     double z0_factor, double kernel_power,
+                                                     const double *m_dev, double *kdz_cells_dev,
+                                                     void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_depth_kernels_from_model: handle is NULL");
+    PDST_CHECK_ARG(periods_host && m_dev && kdz_cells_dev,
+                   "pdst_depth_kernels_from_model: NULL pointer argument");
+    PDST_CHECK_ARG(std::isfinite(z0_factor) && z0_factor > 0.0,
+                   "pdst_depth_kernels_from_model: z0_factor must be positive and finite");
+    PDST_CHECK_ARG(std::isfinite(kernel_power),
+                   "pdst_depth_kernels_from_model: kernel_power must be finite");
+    PDST_CHECK_ARG(std::isfinite(h->grid.dz_km) && h->grid.dz_km > 0.0,
+                   "pdst_depth_kernels_from_model: the grid's dz_km must be positive");
+    for (int t = 0; t < h->n_periods; ++t)
+        PDST_CHECK_ARG(std::isfinite(periods_host[t]) && periods_host[t] > 0.0,
+                       "pdst_depth_kernels_from_model: period %d must be positive and finite", t);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf per;
+    PDST_TRY(per.alloc(sizeof(double) * h->n_periods));
+    PDST_CUDA(cudaMemcpyAsync(per.p, periods_host, sizeof(double) * h->n_periods,
+                              cudaMemcpyHostToDevice, s));
+    const int64_t work = (int64_t)h->H * h->n_periods;
+    k_kernels_from_model<<<grid_for(work, 128, h->device), 128, 0, s>>>(
+        h->H, h->nz, h->n_periods, per.as<double>(), z0_factor, kernel_power, h->grid.dz_km,
+        m_dev, kdz_cells_dev);
+    PDST_CUDA(cudaGetLastError());
+    PDST_CUDA(cudaStreamSynchronize(s));   // the period copy is released on return
+    return PDST_OK;
+}
+
+extern "C" pdst_status pdst_set_depth_kernels(pdst_handle_t h, const double *kdz_cells_dev,
+                                              void *stream) {
+    PDST_CHECK_ARG(h != nullptr, "pdst_set_depth_kernels: handle is NULL");
+    PDST_CHECK_ARG(kdz_cells_dev != nullptr, "pdst_set_depth_kernels: kdz_cells is NULL");
+    if (!h->has_lengths) {
+        set_error("pdst_set_depth_kernels: the handle was built without keep_lengths");
+        return PDST_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nnz = h->nnz;
+    if (!nnz) return PDST_OK;
+    DevBuf v64_tmp;
+    double *v64 = h->vals[PDST_F64].present ? h->vals[PDST_F64].csr.as<double>() : nullptr;
+    if (h->vals[PDST_DF64].present && !v64) {
+        PDST_TRY(v64_tmp.alloc(sizeof(double) * nnz));
+        v64 = v64_tmp.as<double>();
+    }
+    k_expand_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
+        h->U, h->nz, h->run_len.as<double>(), h->run_row.as<int32_t>(),
+        h->row_period.as<int32_t>(), nullptr, h->row_cells.as<int32_t>(), kdz_cells_dev,
+        h->n_periods, v64, h->vals[1].present ? h->vals[1].csr.as<float>() : nullptr,
+        h->vals[2].present ? h->vals[2].csr.as<__nv_bfloat16>() : nullptr);
+    PDST_CUDA(cudaGetLastError());
+    if (h->vals[PDST_DF64].present) {
+        k_split_values<<<grid_for(nnz, 256, h->device), 256, 0, s>>>(
+            nnz, v64, h->vals[PDST_DF64].csr.as<dfl>());
+        PDST_CUDA(cudaGetLastError());
+    }
+    PDST_TRY(transposed_value_copies(h, h->run_pos.as<int64_t>(), s));
+    PDST_CUDA(cudaStreamSynchronize(s));
     return PDST_OK;
 }

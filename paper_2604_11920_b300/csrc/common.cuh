@@ -74,6 +74,14 @@ struct DevBuf {
         return PDST_OK;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
+    // take over o's memory (o ends empty)
+    void take(DevBuf &o) {
+        release();
+        p = o.p;
+        bytes = o.bytes;
+        o.p = nullptr;
+        o.bytes = 0;
+    }
 };
 
 // ------------------------------------------------------------- LSQR state
@@ -179,6 +187,12 @@ struct pdst_handle {
     pdst::DevBuf col_ptr;      // int64 [n+1]
     pdst::DevBuf row_idx;      // int32 [nnz]
     pdst::ValueSet vals[4];    // by pdst_dtype
+
+    // kept with pdst_build_opts.keep_lengths, for pdst_set_depth_kernels
+    pdst::DevBuf run_len;      // double [U]  ray length (or node coefficient) of each run
+    pdst::DevBuf run_row;      // int32 [U]   row of each run
+    pdst::DevBuf run_pos;      // int64 [U]   position of each run in the blocked CSC layout
+    bool has_lengths = false;
 
     pdst::DevBuf colscale;     // double [n] right diagonal scaling D
     bool has_colscale = false;

@@ -43,7 +43,7 @@ class Grid(ctypes.Structure):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("value_dtypes", ctypes.c_uint32), ("formats", ctypes.c_uint32),
                 ("kdz_cells", ctypes.c_void_p), ("interp", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("keep_lengths", ctypes.c_int32)]
 
 
 class LsqrOpts(ctypes.Structure):
@@ -61,6 +61,22 @@ class BatchedOpts(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("kblock", ctypes.c_int32),
                 ("chosen_tile_rows", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("tune_ms", ctypes.c_double * 4)]
+
+
+class OuterOpts(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("rms_tol", ctypes.c_double), ("min_decrease", ctypes.c_double),
+                ("z0_factor", ctypes.c_double), ("kernel_power", ctypes.c_double),
+                ("inner", LsqrOpts)]
+
+
+class OuterInfo(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int32), ("reason", ctypes.c_int32),
+                ("inner_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rms_first", ctypes.c_double), ("rms_final", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class LsqrInfo(ctypes.Structure):
@@ -110,6 +126,11 @@ SIGNATURES = {
     "pdst_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
     "pdst_lsqr_batched": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, _i32, _d, _i32, _vp,
                                  ctypes.POINTER(LsqrInfo), ctypes.POINTER(BatchedOpts), _vp]),
+    "pdst_depth_kernels_from_model": (_i32, [_vp, _vp, _d, _d, _vp, _vp, _vp]),
+    "pdst_set_depth_kernels": (_i32, [_vp, _vp, _vp]),
+    "pdst_outer_opts_default": (None, [ctypes.POINTER(OuterOpts)]),
+    "pdst_outer_loop": (_i32, [_vp, _vp, _vp, _d, _d, _i32, _d, ctypes.POINTER(OuterOpts), _vp,
+                               _vp, ctypes.POINTER(OuterInfo), _vp]),
     "pdst_last_error_string": (ctypes.c_char_p, []),
     "pdst_version": (_i32, []),
 }
@@ -310,6 +331,50 @@ class Handle:
         _check(load().pdst_precond_features(self.ptr, _np_ptr(lp), _dev_ptr(f), _stream(stream)))
         return f
 
+    def depth_kernels_from_model(self, periods, m, z0_factor=1.2, kernel_power=1.0,
+                                 out=None, stream=None):
+        """pdst_depth_kernels_from_model: (nx*ny, T, nz) float64 CUDA tensor."""
+        import torch
+        per = np.ascontiguousarray(periods, dtype=np.float64)
+        T = per.shape[0]
+        H = self.grid.nx * self.grid.ny
+        if out is None:
+            out = torch.empty((H, T, self.grid.nz), dtype=torch.float64, device="cuda")
+        _check(load().pdst_depth_kernels_from_model(
+            self.ptr, _np_ptr(per), float(z0_factor), float(kernel_power),
+            _dev_ptr(m, self.n, torch.float64, "m"),
+            _dev_ptr(out, H * T * self.grid.nz, torch.float64, "out"), _stream(stream)))
+        return out
+
+    def set_depth_kernels(self, kdz_cells, stream=None):
+        import torch
+        _check(load().pdst_set_depth_kernels(self.ptr, _dev_ptr(kdz_cells, None, torch.float64,
+                                                                "kdz_cells"), _stream(stream)))
+
+    def outer_loop(self, d_obs, periods, w, lam, itmax, tol, max_outer=8, rms_tol=0.0,
+                   min_decrease=0.01, z0_factor=1.2, kernel_power=1.0, m_out=None,
+                   stream=None, **inner_kw):
+        """pdst_outer_loop: returns (m, rms history (numpy), info dict)."""
+        import torch
+        per = np.ascontiguousarray(periods, dtype=np.float64)
+        if m_out is None:
+            m_out = torch.empty(self.n, dtype=torch.float64, device=d_obs.device)
+        o = OuterOpts()
+        load().pdst_outer_opts_default(ctypes.byref(o))
+        o.max_outer, o.rms_tol, o.min_decrease = int(max_outer), float(rms_tol), \
+            float(min_decrease)
+        o.z0_factor, o.kernel_power = float(z0_factor), float(kernel_power)
+        o.inner = lsqr_opts(**inner_kw)
+        hist = np.zeros(int(max_outer) + 1)
+        info = OuterInfo()
+        _check(load().pdst_outer_loop(self.ptr, _dev_ptr(d_obs, self.m, torch.float64, "d_obs"),
+                                      _np_ptr(per), float(w), float(lam), int(itmax), float(tol),
+                                      ctypes.byref(o), _dev_ptr(m_out, self.n, torch.float64,
+                                                                "m_out"),
+                                      _np_ptr(hist), ctypes.byref(info), _stream(stream)))
+        inf = info.as_dict()
+        return m_out, hist[: inf["updates"] + 1], inf
+
     def set_col_scaling(self, D=None, w=0.0, lam=0.0, stream=None):
         import torch
         p = ctypes.c_void_p(None) if D is None else _dev_ptr(D, self.n, torch.float64, "D")
@@ -317,7 +382,8 @@ class Handle:
 
 
 def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=("f64", "f32"),
-            formats=("element", "blocked"), stream=None, kdz_cells=None, interp=0) -> Handle:
+            formats=("element", "blocked"), stream=None, kdz_cells=None, interp=0,
+            keep_lengths=False) -> Handle:
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 6)
     row_period = np.ascontiguousarray(row_period, dtype=np.int32)
     kdz = np.ascontiguousarray(kdz, dtype=np.float64)
@@ -328,7 +394,7 @@ def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=(
         if kc.shape != (nx * ny, int(n_periods), nz):
             raise ValueError("kdz_cells must be (nx*ny, n_periods, nz)")
     opts = BuildOpts(sum(1 << DTYPES[d] for d in dtypes), sum(1 << FORMATS[f] for f in formats),
-                     None if kc is None else kc.ctypes.data, int(interp), 0)
+                     None if kc is None else kc.ctypes.data, int(interp), int(bool(keep_lengths)))
     out = ctypes.c_void_p()
     _check(load().pdst_build_G(ctypes.byref(grid), ctrl.shape[0], _np_ptr(ctrl),
                                _np_ptr(row_period), int(n_periods), _np_ptr(kdz),

@@ -46,7 +46,9 @@ def test_struct_layouts_match_header(lib, tmp_path):
     import subprocess
     from paper_2604_11920_b300 import pdst
     structs = {"pdst_grid": pdst.Grid, "pdst_build_opts": pdst.BuildOpts,
-               "pdst_lsqr_opts": pdst.LsqrOpts, "pdst_lsqr_info": pdst.LsqrInfo}
+               "pdst_lsqr_opts": pdst.LsqrOpts, "pdst_lsqr_info": pdst.LsqrInfo,
+               "pdst_batched_opts": pdst.BatchedOpts, "pdst_outer_opts": pdst.OuterOpts,
+               "pdst_outer_info": pdst.OuterInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdst.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
