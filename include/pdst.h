@@ -305,6 +305,11 @@ typedef struct {
     int32_t chosen_tile_rows; /* out: the tile used by the call */
     int32_t kernel_launches;  /* out: kernels launched by the call (graph nodes included) */
     double tune_ms[4];        /* out: iteration time per autotuner candidate (ms) */
+    int32_t precond;          /* 0 none; 1 each system's right diagonal scaling set by
+                                 pdst_set_col_scaling on its handle: pair (s, j) solves
+                                 A_D = [G D; w L D; lambda_j D] with no recurrence damping and
+                                 returns m = D y (the same minimiser) */
+    int32_t reserved;
 } pdst_batched_opts;
 
 /* Fill *o with the defaults listed above. */

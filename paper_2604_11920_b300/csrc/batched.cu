@@ -31,8 +31,8 @@ namespace {
 constexpr int BT = 256;      // threads per block
 constexpr int RMAX = 16;     // right-hand sides per system (lanes of a half-warp)
 constexpr int LCOLS = 32;    // columns per stencil / update work item
-constexpr int NB = 7;        // work buffers per system: U, V, X, W, chunk sums, chunk counters,
-                             // cell sums
+constexpr int NB = 8;        // work buffers per system: U, V, X, W, chunk sums, chunk counters,
+                             // cell sums, scaled V
 
 template <class VT, class ST> struct BSys {
     int64_t m;
@@ -53,8 +53,11 @@ template <class VT, class ST> struct BSys {
     ST *chunk_part;   // adjoint work items x nz x RMAX partial sums
     unsigned *cell_done;       // H finished-chunk counters
     double *cell_ss;           // H x RMAX: sum of v^2 of cells finished across several items
-    ST *U;            // (m + n) x RS, right-hand side fastest (padding lanes stay 0)
+    ST *U;            // (m + n [+ n]) x RS, right-hand side fastest (padding lanes stay 0)
     ST *V;            // n x RS, right-hand side fastest (padding lanes stay 0)
+    ST *Vs;           // n x RS: D o V with a right scaling, else V itself
+    const double *D;  // right diagonal scaling D (n) or nullptr
+    int32_t lamr;     // 1: the lambda_j D rows are appended (scaled form)
     double *X, *W;    // n x R
     const double *d;  // m x R
     LsqrScalars *sc;  // R
@@ -109,15 +112,17 @@ struct WarpSum {
 struct Col {
     bool act;
     double alpha, beta;
+    double lam;       // lambda of the appended lambda D rows (scaled form), else 0
 };
 
 __device__ __forceinline__ Col col_state(const LsqrScalars *sc, int j, int R) {
-    Col c{false, 0.0, 0.0};
+    Col c{false, 0.0, 0.0, 0.0};
     if (j < R) {
         const LsqrScalars &s = sc[j];
         c.act = !(s.done | s.istop);
         c.alpha = s.alpha;
         c.beta = s.beta;
+        c.lam = s.lam_rows;
     }
     return c;
 }
@@ -168,7 +173,9 @@ __global__ void __launch_bounds__(BT) k_binit(BSys<VT, ST> *sys, int nsys, const
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 for (int64_t c = c0 + half; c < c1; c += 2) {
                     S.U[(S.m + c) * S.RS + j] = (ST)0;
+                    if (S.lamr) S.U[(S.m + S.n + c) * S.RS + j] = (ST)0;
                     S.V[c * S.RS + j] = (ST)0;
+                    S.Vs[c * S.RS + j] = (ST)0;
                     S.X[c * R + j] = 0.0;
                     S.W[c * R + j] = 0.0;
                 }
@@ -226,7 +233,7 @@ __device__ __forceinline__ void fwd_g_item(const BSys<VT, ST> &S, int64_t li, in
         if constexpr (NZC > 0) {
             constexpr int NI = NZC / 4;   // depths per lane (k0, k0 + 4, ...)
             const VT *vrow = S.val + e0 * NZC + k0;
-            const ST *vb = S.V + 4 * g + k0 * 16;
+            const ST *vb = S.Vs + 4 * g + k0 * 16;
             for (int e = 0; e < nmax; e += 2) {
                 const int h0 = __shfl_sync(FULL, pick4(cc, e >> 4), (half << 4) | (e & 15));
                 const int h1 =
@@ -264,7 +271,7 @@ __device__ __forceinline__ void fwd_g_item(const BSys<VT, ST> &S, int64_t li, in
                 if (e >= nrun) continue;
                 if (e >= 64) h = __ldg(S.row_cells + e0 + e);
                 const VT *v = S.val + (e0 + e) * nz;
-                const ST *xb = S.V + (int64_t)h * nz * RS + 4 * g;
+                const ST *xb = S.Vs + (int64_t)h * nz * RS + 4 * g;
                 for (int k = k0; k < nz; k += kst) {
                     const AT a = (AT)ldval(v + k);
                     ST xv[4];
@@ -326,12 +333,18 @@ __global__ void __launch_bounds__(BT, 4) k_bfwd(BSys<VT, ST> *sys, int nsys, con
                 const int64_t c1 = c0 + LCOLS < S.n ? c0 + LCOLS : S.n;
                 const AT wsm = (AT)S.w;
                 for (int64_t jc = c0 + half; jc < c1; jc += 2) {
-                    const AT lap = laplace_strided<AT, ST>(S.V, jc, RS, jj, S.nx, S.ny, nz);
+                    const AT lap = laplace_strided<AT, ST>(S.Vs, jc, RS, jj, S.nx, S.ny, nz);
                     if (c.act) {
                         ST *up = S.U + (S.m + jc) * RS + j;
                         const AT u = wsm * lap * ia - cu * *up;
                         *up = u;
                         ss += (double)u * (double)u;
+                        if (S.lamr) {   // lambda_j D v rows (the same order as the single solve)
+                            ST *ul = S.U + (S.m + S.n + jc) * RS + j;
+                            const AT u2 = (AT)c.lam * (AT)S.Vs[jc * RS + j] * ia - cu * *ul;
+                            *ul = u2;
+                            ss += (double)u2 * (double)u2;
+                        }
                     }
                 }
             }
@@ -479,13 +492,14 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
     double ss4[4] = {0.0, 0.0, 0.0, 0.0};
     if (finish && sub == 0) {
         bool upd[4];
-        AT ib[4], cv[4];
+        AT ib[4], cv[4], lr[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const Col c = col_state(S.sc, 4 * g + b, S.R);
             upd[b] = c.act && (init || c.beta > 0.0);
             ib[b] = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
             cv[b] = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
+            lr[b] = (AT)c.lam;
         }
         const AT wsm = (AT)S.w;
 #pragma unroll
@@ -494,12 +508,16 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
             AT lap[4];
             laplace4<AT, ST>(S.U + S.m * 16, jc, g, S.nx, S.ny, NZC, lap);
             ST *vp = S.V + jc * 16 + 4 * g;
+            const AT dj = S.D ? (AT)S.D[jc] : (AT)1;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 if (!upd[b]) continue;
-                const AT sv = acc[a][b] + wsm * lap[b];
+                AT sv = acc[a][b] + wsm * lap[b];
+                if (S.lamr) sv += lr[b] * (AT)S.U[(S.m + S.n + jc) * 16 + 4 * g + b];
+                if (S.D) sv *= dj;
                 const AT v = init ? sv * ib[b] : sv * ib[b] - cv[b] * vp[b];
                 vp[b] = v;
+                if (S.D) S.Vs[jc * 16 + 4 * g + b] = dj * v;
                 ss4[b] += (double)v * (double)v;
             }
         }
@@ -602,11 +620,15 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
         for (int k = 0; k < BNZ; ++k) {
             if (k >= nz) continue;
             const int64_t jc = (int64_t)h * nz + k;
-            const AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * RS, jc, RS, j, S.nx,
-                                                                 S.ny, nz);
+            AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * RS, jc, RS, j, S.nx,
+                                                           S.ny, nz);
+            if (S.lamr) sv += (AT)c.lam * (AT)S.U[(S.m + S.n + jc) * RS + j];
+            const AT dj = S.D ? (AT)S.D[jc] : (AT)1;
+            if (S.D) sv *= dj;
             ST *vp = S.V + jc * RS + j;
             const AT v = init ? sv * ib : sv * ib - cv * *vp;
             *vp = v;
+            if (S.D) S.Vs[jc * RS + j] = dj * v;
             ss += (double)v * (double)v;
         }
     }
@@ -687,6 +709,15 @@ __global__ void __launch_bounds__(BT) k_bupd(BSys<VT, ST> *sys, int nsys, const 
         ws.add(ss, s, partial, gw, nw);
     }
     ws.finish(partial, nsys, gw, nw);
+}
+
+// m = D o x (scaled form) or x, n x R per system.
+__global__ void k_bfinal(int64_t n, int R, const double *__restrict__ D, const double *__restrict__ X,
+                         double *m_out) {
+    const int64_t total = n * R;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m_out[i] = D ? D[i / R] * X[i] : X[i];
 }
 
 // One block of 256 threads per system: thread (l, j) sums the partials of the
@@ -785,8 +816,9 @@ struct BatchKey {
     std::vector<uint64_t> hs;   // handle uids
     std::vector<int32_t> nrhs;
     int dtype;
+    int precond;
     bool operator<(const BatchKey &o) const {
-        return std::tie(hs, nrhs, dtype) < std::tie(o.hs, o.nrhs, o.dtype);
+        return std::tie(hs, nrhs, dtype, precond) < std::tie(o.hs, o.nrhs, o.dtype, o.precond);
     }
 };
 
@@ -847,6 +879,7 @@ template <class VT, class ST> struct Batched {
 
     static pdst_status prepare(BatchWork *bw, const std::vector<pdst_handle *> &hs,
                                const int32_t *nrhs, int dtype, int TR, cudaStream_t s) {
+        const bool scaled = bw->key.precond != 0;
         const int nsys = (int)hs.size();
         std::vector<Sys> d(nsys);
         std::vector<int64_t> nf;
@@ -873,20 +906,25 @@ template <class VT, class ST> struct Batched {
                 pdst_handle *h = hs[i];
                 const int R = nrhs[i];
                 DevBuf *U = new DevBuf, *V = new DevBuf, *X = new DevBuf, *W = new DevBuf;
-                DevBuf *CP = new DevBuf, *CD = new DevBuf, *CS = new DevBuf;
-                bw->bufs.insert(bw->bufs.end(), {U, V, X, W, CP, CD, CS});
+                DevBuf *CP = new DevBuf, *CD = new DevBuf, *CS = new DevBuf, *VS = new DevBuf;
+                bw->bufs.insert(bw->bufs.end(), {U, V, X, W, CP, CD, CS, VS});
                 const int64_t csb = sizeof(double) * std::max<int64_t>((int64_t)h->H * RMAX, 1);
                 PDST_TRY(CS->alloc(csb));
                 PDST_CUDA(cudaMemsetAsync(CS->p, 0, csb, s));
                 PDST_TRY(CP->alloc(sizeof(ST) * std::max<int64_t>(h->n_adj * h->nz * RMAX, 1)));
                 PDST_TRY(CD->alloc(sizeof(unsigned) * std::max<int32_t>(h->H, 1)));
                 PDST_CUDA(cudaMemsetAsync(CD->p, 0, sizeof(unsigned) * std::max<int32_t>(h->H, 1), s));
-                const int64_t ubytes = sizeof(ST) * (h->m + h->n) * v_stride(R);
+                const int64_t ubytes =
+                    sizeof(ST) * (h->m + h->n + (scaled ? h->n : 0)) * v_stride(R);
                 PDST_TRY(U->alloc(ubytes));
                 PDST_CUDA(cudaMemsetAsync(U->p, 0, ubytes, s));
                 const int64_t vbytes = sizeof(ST) * std::max<int64_t>((int64_t)h->n * v_stride(R), 1);
                 PDST_TRY(V->alloc(vbytes));
                 PDST_CUDA(cudaMemsetAsync(V->p, 0, vbytes, s));
+                if (scaled) {
+                    PDST_TRY(VS->alloc(vbytes));
+                    PDST_CUDA(cudaMemsetAsync(VS->p, 0, vbytes, s));
+                }
                 PDST_TRY(X->alloc(sizeof(double) * (int64_t)h->n * R));
                 PDST_TRY(W->alloc(sizeof(double) * (int64_t)h->n * R));
             }
@@ -923,6 +961,9 @@ template <class VT, class ST> struct Batched {
             q.valB = h->vals[dtype].bcsc.as<VT>();
             q.U = bw->bufs[NB * i]->as<ST>();
             q.V = bw->bufs[NB * i + 1]->as<ST>();
+            q.Vs = scaled ? bw->bufs[NB * i + 7]->as<ST>() : q.V;
+            q.D = scaled ? h->colscale.as<double>() : nullptr;
+            q.lamr = scaled ? 1 : 0;
             q.X = bw->bufs[NB * i + 2]->as<double>();
             q.W = bw->bufs[NB * i + 3]->as<double>();
             q.chunk_part = bw->bufs[NB * i + 4]->as<ST>();
@@ -1095,10 +1136,16 @@ template <class VT, class ST> struct Batched {
             PDST_CUDA(cudaGraphLaunch(exec, s));
             launches += 6 * kblock;
         }
-        for (int i = 0; i < nsys; ++i)
-            PDST_CUDA(cudaMemcpyAsync(m_out[i], bw->bufs[NB * i + 2]->p,
-                                      sizeof(double) * (int64_t)hs[i]->n * nrhs[i],
-                                      cudaMemcpyDeviceToDevice, s));
+        for (int i = 0; i < nsys; ++i) {
+            const int64_t n = hs[i]->n;
+            const unsigned g = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((n * nrhs[i] + BT - 1) / BT, (int64_t)num_sms(device) * 8));
+            k_bfinal<<<g, BT, 0, s>>>(n, nrhs[i],
+                                      bw->key.precond ? hs[i]->colscale.as<double>() : nullptr,
+                                      bw->bufs[NB * i + 2]->as<double>(), m_out[i]);
+        }
+        PDST_CUDA(cudaGetLastError());
+        launches += nsys;
         PDST_CUDA(cudaMemcpyAsync(bw->h_scal, bw->scal.p, sizeof(LsqrScalars) * nsys * RMAX,
                                   cudaMemcpyDeviceToHost, s));
         PDST_CUDA(cudaStreamSynchronize(s));
@@ -1118,6 +1165,8 @@ extern "C" void pdst_batched_opts_default(pdst_batched_opts *o) {
     o->chosen_tile_rows = 0;
     o->kernel_launches = 0;
     for (int i = 0; i < 4; ++i) o->tune_ms[i] = 0.0;
+    o->precond = 0;
+    o->reserved = 0;
 }
 
 extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, const int32_t *nrhs,
@@ -1159,6 +1208,15 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
     pdst_batched_opts_default(&local);
     if (opts) local = *opts;
     const int kblock = local.kblock > 0 ? local.kblock : 8;
+    PDST_CHECK_ARG(local.precond == 0 || local.precond == 1,
+                   "pdst_lsqr_batched: unknown precond %d", local.precond);
+    if (local.precond)
+        for (int i = 0; i < nsys; ++i)
+            if (!hs[i]->has_colscale) {
+                set_error("pdst_lsqr_batched: precond = 1 needs pdst_set_col_scaling on handle %d",
+                          i);
+                return PDST_ERR_STATE;
+            }
     PDST_CHECK_ARG(kblock <= 256, "pdst_lsqr_batched: kblock must be <= 256");
     PDST_CHECK_ARG(local.tile_rows >= 0 && local.tile_rows <= 4096,
                    "pdst_lsqr_batched: tile_rows out of range");
@@ -1169,7 +1227,10 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
             LsqrScalars &q = init[(size_t)i * RMAX + j];
             q = LsqrScalars{};
             q.cs2 = -1.0;
-            q.damp = j < nrhs[i] ? lambda[i][j] : 0.0;
+            const double lam = j < nrhs[i] ? lambda[i][j] : 0.0;
+            // scaled form: lambda_j D rows in the operator, no recurrence damping
+            q.damp = local.precond ? 0.0 : lam;
+            q.lam_rows = local.precond ? lam : 0.0;
             q.atol = tol;
             q.btol = tol;
             q.ctol = 1e-8;
@@ -1179,7 +1240,8 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
         }
 
     std::lock_guard<std::mutex> lock(g_batch_mutex);
-    BatchKey key{std::vector<uint64_t>(nsys), std::vector<int32_t>(nrhs, nrhs + nsys), dtype};
+    BatchKey key{std::vector<uint64_t>(nsys), std::vector<int32_t>(nrhs, nrhs + nsys), dtype,
+                 local.precond};
     for (int i = 0; i < nsys; ++i) key.hs[i] = hs[i]->uid;
     if (!g_batch || g_batch->key < key || key < g_batch->key) {
         delete g_batch;

@@ -60,7 +60,8 @@ class LsqrOpts(ctypes.Structure):
 class BatchedOpts(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("kblock", ctypes.c_int32),
                 ("chosen_tile_rows", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double * 4)]
+                ("tune_ms", ctypes.c_double * 4), ("precond", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class OuterOpts(ctypes.Structure):
@@ -411,7 +412,7 @@ def build_G_problem(p, **kw) -> Handle:
 
 
 def lsqr_batched(handles, ds, w, lams, itmax, tol, dtype="f32", tile_rows=0, kblock=8,
-                 m_outs=None, stream=None):
+                 m_outs=None, stream=None, precond=0):
     """pdst_lsqr_batched.  ds[s]: (m_s, R_s) float64 CUDA tensors (right-hand
     sides in columns); lams[s]: R_s damping values.  Returns (m_outs, infos,
     opts) with m_outs[s] of shape (n_s, R_s)."""
@@ -435,7 +436,7 @@ def lsqr_batched(handles, ds, w, lams, itmax, tol, dtype="f32", tile_rows=0, kbl
     infos = (LsqrInfo * sum(R))()
     o = BatchedOpts()
     lib.pdst_batched_opts_default(ctypes.byref(o))
-    o.tile_rows, o.kblock = int(tile_rows), int(kblock)
+    o.tile_rows, o.kblock, o.precond = int(tile_rows), int(kblock), int(precond)
     _check(lib.pdst_lsqr_batched(nsys, hs, nr, dp, wv, lp, int(itmax), float(tol), DTYPES[dtype],
                                  mp, infos, ctypes.byref(o), _stream(stream)))
     out_infos, k = [], 0

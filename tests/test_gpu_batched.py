@@ -181,3 +181,63 @@ def test_nzc_paths_converged_match_oracle(nzc):
             e32 = rel(m32[:, j].cpu().numpy(), ref.x)
             e_or = rel(same.x, ref.x)
             assert e32 <= 2.0 * e_or + 1e-3, (p.nz, j, e32, e_or)
+
+
+# ------------------------------------------------ batched with right scaling
+# precond = 1: each system's handle scaling D (here the oracle's column norms,
+# so both sides apply the same operator), pair (s, j) on
+# [G D; w L D; lambda_j D] with no recurrence damping, m = D y (reading of the
+# scaled form: the same minimiser as the damped problem).
+
+def _set_oracle_scaling(b, hs):
+    Ds = []
+    for (p, G, GT, D, lams), h in zip(b, hs):
+        c = oracle.aug_colnorm2(GT, p.nx, p.ny, p.nz, p.w, p.lam)
+        Dc = 1.0 / np.sqrt(c)
+        h.set_col_scaling(to_dev(Dc))
+        Ds.append(Dc)
+    return Ds
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_scaled_batched_fixed_k_match_oracle(nzc, k):
+    b, hs = nzc
+    Ds = _set_oracle_scaling(b, hs)
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, *_ in b], [l for *_, l in b], k, 0.0,
+                                       dtype="f64", tile_rows=8, precond=1)
+    for (p, G, GT, D, lams), Dc, mo, inf in zip(b, Ds, outs, infos):
+        got = mo.cpu().numpy()
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k, D=Dc, lam_rows=lams[j])
+            assert inf[j]["iters"] == k
+            assert rel(got[:, j], Dc * ref.x) < 1e-10, (p.nz, j, k)
+
+
+def test_scaled_batched_converges_faster_to_the_same_minimiser(nzc):
+    b, hs = nzc
+    Ds = _set_oracle_scaling(b, hs)
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    w = [p.w for p, *_ in b]
+    lams = [l for *_, l in b]
+    o_s, i_s, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32", precond=1)
+    o_u, i_u, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32")
+    it_s = sum(inf["iters"] for row in i_s for inf in row)
+    it_u = sum(inf["iters"] for row in i_u for inf in row)
+    print(f"FP32 batched, tol 1e-6: scaled {it_s} iterations, unscaled {it_u}")
+    assert it_s < it_u
+    for (p, G, GT, D, lj), Dc, ms, inf in zip(b, Ds, o_s, i_s):
+        for j in (0, D.shape[1] // 2, D.shape[1] - 1):
+            grid = (p.nx, p.ny, p.nz)
+            ref = oracle.lsqr(G, GT, grid, p.w, lj[j], D[:, j], atol=1e-12, btol=1e-12,
+                              itmax=50000)
+            same = oracle.lsqr(G, GT, grid, p.w, 0.0, D[:, j], atol=1e-6, btol=1e-6,
+                               itmax=50000, D=Dc, lam_rows=lj[j])
+            assert inf[j]["istop"] in (1, 2)
+            e32 = rel(ms[:, j].cpu().numpy(), ref.x)
+            e_or = rel(Dc * same.x, ref.x)
+            assert e32 <= 2.0 * e_or + 1e-3, (p.nz, j, e32, e_or)
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
+        fresh = pdst.build_G_problem(b[0][0], dtypes=("f32",), formats=("blocked",))
+        pdst.lsqr_batched([fresh], [ds[0]], [1.0], [lams[0]], 10, 1e-6, dtype="f32", precond=1)
