@@ -3,21 +3,29 @@
 
 Workload (default): the 64 x 64 x 16 system (65,536 unknowns; 120 stations,
 7,140 pairs x 24 periods = 171,360 rows; Bezier rays; Gaussian-blob model,
-2 % noise; w = 2, lambda = 0.05; tol 1e-6), synthetic inputs from the seeded
-generator.  One step = one LSQR solve to tolerance on the device-resident G
-(forward product, adjoint product, FP64 recurrence and x/w update, all in the
-library's kernels, replayed from a CUDA graph).  The G assembly is timed
-separately (`build_G_s`).
+2 % noise; w = 2, lambda = 0.05), synthetic inputs from the seeded generator.
 
-Reported beside the headline: the plain FP64 GPU LSQR on the same system (FP64
-values and vectors, element CSR/CSC, no scaling, graph on), the model error of
-both against an FP64 reference solve, a per-kernel roofline from CUDA events,
-the end-to-end time through the host entry point, and the FP64 CPU oracle
-timed on this machine's cores on a bounded sample.
+One step = one solve of the chosen form (FP32 values and vectors, FP64
+scalars, column-norm scaling computed inside the step) to within 1e-4
+relative model error of the FP64 oracle's converged solution (stored in
+tests/golden by a script that calls only the oracle): the FP32 solve to tol
+1e-6, then refinement sweeps with FP32 values on the FP64 residual, their
+tolerance the loosest rung of a fixed ladder that reaches the target (found
+once, untimed).  Every step runs in the library's kernels on device-resident
+G, replayed from CUDA graphs.  The G assembly is timed separately.
+
+Reported beside the headline: the plain FP64 GPU LSQR (FP64 values and
+vectors, element CSR/CSC, no scaling) at the same target and its own
+per-kernel roofline; the learned scaling at the same target; both forms at
+tol 1e-6 (one solve); LSMR; the damping sweep; the batched workload; compact
+records of the paper-shaped and 100 x 100 x 20 systems; the per-kernel
+roofline of the chosen form from CUDA events; the end-to-end time through
+the host entry point; and the FP64 CPU oracle timed on this machine's cores
+on a bounded sample, scaled to the iterations the oracle itself needs.
 
 `--impl reference` times the FP64 CPU oracle alone (the comparison arm).
-Multi-GPU (torchrun): every rank solves its own system (seed + rank); no data
-moves between ranks ("replicas only").
+Multi-GPU (torchrun): every rank solves its own system (seed + 1000 rank);
+no data moves between ranks ("replicas only").
 """
 from __future__ import annotations
 
@@ -50,7 +58,9 @@ FORMS = {
 }
 PLAIN = "f64-element"
 MODEL_PATH = os.path.join(ROOT, "paper_2604_11920_b300", "precond_mlp.json")
-DEFAULT_FORM = "f32-blocked-learned" if os.path.exists(MODEL_PATH) else "f32-blocked-colnorm"
+# the chosen form: FP32 values with FP64 scalars and column-norm scaling (the
+# learned scaling is measured beside it on the same target)
+DEFAULT_FORM = "f32-blocked-colnorm"
 ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
 TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10)
 REFINE_DTYPE = "f32"                  # refinement sweeps of the reduced-precision forms
@@ -77,6 +87,9 @@ def parse_args():
     ap.add_argument("--only-batched", action="store_true",
                     help="print the batched-workload section alone")
     ap.add_argument("--no-lsmr", action="store_true", help="skip the LSMR section")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the compact paper-shaped and 100x100x20 sections of the "
+                         "default (64x64x16) run")
     ap.add_argument("--no-sweep", action="store_true", help="skip the damping-sweep section")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy-matched ladder (skipped by default on "
@@ -251,6 +264,122 @@ def run_ncu_case(args):
     h.close()
 
 
+def load_mref(workload, seed):
+    """The FP64 oracle's converged solution of a workload, stored by a
+    committed script that calls only the oracle (tests/golden/make_mref.py);
+    None when there is none for this workload and seed."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"{workload}_mref.npy")
+    meta_path = path[:-4] + ".json"
+    if not (os.path.exists(path) and os.path.exists(meta_path)):
+        return None, None
+    meta = json.load(open(meta_path))
+    if meta.get("seed") != seed:
+        return None, None
+    return np.load(path), meta
+
+
+class System:
+    """One device-resident system of the benchmark with its right-hand side
+    (synthesised on the device with the library's FP64 product) and the
+    solve forms of FORMS."""
+
+    def __init__(self, p, dtypes, formats=("element", "blocked"), params=None):
+        import torch
+
+        from paper_2604_11920_b300 import pdst
+        self.p = p
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self.h = pdst.build_G_problem(p, dtypes=tuple(sorted(set(dtypes))), formats=formats)
+        torch.cuda.synchronize()
+        self.build_s = time.perf_counter() - t0
+        mt = torch.from_numpy(p.m_true).cuda()
+        gm = torch.empty(self.h.m, dtype=torch.float64, device="cuda")
+        self.h.apply_G(mt, gm, dtype="f64")
+        rms = torch.sqrt(torch.mean(gm * gm))
+        self.d = gm + p.noise_frac * rms * torch.from_numpy(p.noise).cuda()
+        self.params = params
+
+    def set_scaling(self, pc):
+        if pc == 1:
+            self.h.set_col_scaling_power(self.p.w, self.p.lam, 1.0)
+        elif pc == 2:
+            from paper_2604_11920_b300.train_precond import learned_scaling
+            learned_scaling(self.h, self.p, self.params)   # features + MLP, inside the step
+
+    def solve(self, form, tol=None, itmax=None, **kw):
+        """One solve of `form`, its scaling computed first (part of the step)."""
+        dt, fm, pc = FORMS[form]
+        self.set_scaling(pc)
+        return self.h.lsqr(self.d, self.p.w, self.p.lam, itmax or self.p.itmax,
+                           self.p.tol if tol is None else tol, dtype=dt, fmt=fm,
+                           precond=1 if pc else 0, **kw)
+
+    def acc_kw(self, form, t):
+        """Solve arguments of the accuracy-matched form at ladder rung t: the
+        plain FP64 form solves to tol t; reduced-precision forms run two-phase
+        (their solve to the workload's tol, then refinement sweeps with FP32
+        values on the FP64 residual to tol t)."""
+        dt = FORMS[form][0]
+        if dt == "f64":
+            return {"tol": t, "itmax": 200000}
+        return {"itmax": 200000, "refine": 3, "refine_dtype": REFINE_DTYPE, "refine_tol": t}
+
+    def close(self):
+        self.h.close()
+
+
+def event_time(stream, fn):
+    """Device time of fn() on `stream` (CUDA events, synchronised on both sides)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def relerr_to(m_ref):
+    import torch
+
+    def f(m):
+        return float(torch.linalg.norm(m - m_ref) / torch.linalg.norm(m_ref))
+    return f
+
+
+def calibrate(S, form, relerr, stream):
+    """Loosest rung of TOL_LADDER at which `form` reaches ACC_TARGET (one timed
+    solve per rung); None if no rung does."""
+    err = None
+    for t in TOL_LADDER:
+        s, r = event_time(stream, lambda: S.solve(form, **S.acc_kw(form, t)))
+        err = relerr(r.m)
+        if err <= ACC_TARGET:
+            return {"tol": t, "s": s, "iters": r.info["iters"], "sweeps": r.info["sweeps"],
+                    "model_error": err}
+    return {"tol": None, "s": None, "model_error": err}
+
+
+def kernel_roofline(S, form, peak, iters=60):
+    """Per-kernel device time (profile mode: CUDA events around each launch of
+    `iters` iterations) and the HBM fraction of each sweep on its
+    algorithmic bytes."""
+    dt, fm, pc = FORMS[form]
+    prof = S.solve(form, itmax=iters, tol=0.0, profile=True, conlim=1e300)
+    pi = max(prof.info["profiled_iters"], 1)
+    kms = {"fwd": prof.info["fwd_ms"] / pi, "adj": prof.info["adj_ms"] / pi,
+           "upd": prof.info["upd_ms"] / pi}
+    ab = algorithmic_bytes(S.h, S.p, dt, fm, pc > 0)
+    gbs = {k: ab[k] / (kms[k] * 1e-3) / 1e9 for k in ("fwd", "adj")}
+    return {"kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
+            "gbs": {k: round(v, 1) for k, v in gbs.items()},
+            "frac_of_hbm": {k: round(v / peak, 4) for k, v in gbs.items()},
+            "bytes": ab, "iters_profiled": pi}
+
+
 def run_pdst(args, rank, world):
     import torch
 
@@ -265,48 +394,60 @@ def run_pdst(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = ("MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks
+                else "fallback 6400 GB/s")
+
     p = make_problem(args.workload, rank)
     dtype, fmt, precond = FORMS[args.form]
-    dtypes = sorted({"f64", "df64", "f32", dtype})   # f32, df64: the refinement sweeps
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h = pdst.build_G_problem(p, dtypes=tuple(dtypes))
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-
-    # right-hand side d = G m_true + 2 % noise (input synthesis on the device)
-    mt = torch.from_numpy(p.m_true).cuda()
-    gm = torch.empty(h.m, dtype=torch.float64, device="cuda")
-    h.apply_G(mt, gm, dtype="f64")
-    rms = torch.sqrt(torch.mean(gm * gm))
-    d = gm + p.noise_frac * rms * torch.from_numpy(p.noise).cuda()
-    itmax = p.itmax
     params = None
-    if precond == 2:
-        from paper_2604_11920_b300.train_precond import learned_scaling, load_params
-        params = load_params(MODEL_PATH)
+    if precond == 2 or os.path.exists(MODEL_PATH):
+        from paper_2604_11920_b300.train_precond import load_params
+        params = load_params(MODEL_PATH) if os.path.exists(MODEL_PATH) else None
+    S = System(p, {"f64", "df64", "f32", dtype}, params=params)
+    h = S.h
 
-    def set_scaling(pc):
-        if pc == 1:
-            h.set_col_scaling_power(p.w, p.lam, 1.0)
-        elif pc == 2:
-            learned_scaling(h, p, params)     # features + MLP, inside the step
+    # ---- the reference solution: the oracle's, stored; else the GPU's FP64 solve
+    m_ref_np, ref_meta = load_mref(args.workload, p.seed)
+    if m_ref_np is not None:
+        m_ref = torch.from_numpy(m_ref_np).cuda()
+        ref_desc = {"source": "FP64 CPU oracle (stored, tests/golden)", "tol": ref_meta["atol"],
+                    "iters": ref_meta["iters"], "istop": ref_meta["istop"]}
+    else:
+        ref = h.lsqr(S.d, p.w, p.lam, 200000, args.ref_tol, dtype="f64", fmt="element")
+        m_ref = ref.m.clone()
+        ref_desc = {"source": "GPU plain FP64 solve (no oracle solution stored for this "
+                              "workload)", "tol": args.ref_tol, "iters": ref.info["iters"],
+                    "istop": ref.info["istop"]}
+    relerr = relerr_to(m_ref)
 
-    def solve(form, tol=p.tol, **kw):
-        dt, fm, pc = FORMS[form]
-        set_scaling(pc)
-        return h.lsqr(d, p.w, p.lam, itmax, tol, dtype=dt, fmt=fm, precond=1 if pc else 0, **kw)
+    # ---- headline: time to within ACC_TARGET of the reference, chosen form
+    headline_acc = not args.no_accuracy
+    cal = calibrate(S, args.form, relerr, stream) if headline_acc else None
+    if cal is not None and cal["tol"] is not None:
+        kw = S.acc_kw(args.form, cal["tol"])
+        step_desc = (f"one solve to within {ACC_TARGET:g} relative model error of the "
+                     f"reference: {dtype} solve to tol {p.tol:g}, then refinement sweeps with "
+                     f"FP32 values on the FP64 residual to tol {cal['tol']:g} (loosest rung of "
+                     "the tolerance ladder that reaches it); scaling computed inside the step")
+        metric_kind = "time_to_1e-4"
+    else:
+        kw = {}
+        step_desc = f"one LSQR solve to tol {p.tol:g} on device-resident G (graph replay)"
+        metric_kind = f"time_to_tol_{p.tol:g}"
 
-    def timed(form, steps, warmup, **kw):
+    def timed(form, steps, warmup, **skw):
         for _ in range(warmup):
-            solve(form, **kw)
+            S.solve(form, **skw)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         e0.record(stream)
         for _ in range(steps):
-            r = solve(form, **kw)
+            r = S.solve(form, **skw)
             launches += r.info["kernel_launches"]
         e1.record(stream)
         torch.cuda.synchronize()
@@ -315,206 +456,228 @@ def run_pdst(args, rank, world):
         return ms, r, launches
 
     with ClockSampler(dev, enabled=not args.no_clocks) as clk:
-        ms, res, launches = timed(args.form, args.steps, args.warmup)
+        ms, res, launches = timed(args.form, args.steps, args.warmup, **kw)
     clocks = clk.summary()
     if args.only_solve:
         if rank == 0:
             print(json.dumps({"form": args.form, "ms_per_solve": ms, "iters": res.info["iters"],
-                              "istop": res.info["istop"]}))
+                              "istop": res.info["istop"], "model_error": relerr(res.m)}))
         return
-
+    headline_err = relerr(res.m)
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": dtype, "data": "synthetic (seeded generator; no dataset)"}
-    m_chosen = res.m.clone()
-    it_chosen = res.info["iters"]
 
-    # plain FP64 GPU LSQR on the same system
-    if args.form != PLAIN:
-        ms_plain, res_plain, _ = timed(PLAIN, max(1, min(args.steps, 3)), 1)
-    else:
-        ms_plain, res_plain = ms, res
-    m_plain = res_plain.m.clone()
-    # FP64 reference solution: plain form at tol REF_TOL (its iteration count is reported)
-    ref = h.lsqr(d, p.w, p.lam, 200000, args.ref_tol, dtype="f64", fmt="element")
-
-    def relerr(a):
-        return float(torch.linalg.norm(a - ref.m) / torch.linalg.norm(ref.m))
-
-    # time to reach the FP64 reference within ACC_TARGET.  Plain FP64: loosest
-    # tolerance of the ladder that gets there.  Reduced-precision forms: one
-    # solve stalls near the FP32 accuracy limit (large-residual problem), so
-    # they run two-phase: the form's solve to tol, then refinement sweeps on the
-    # FP64 residual (FP32 values; each sweep starts from the exact residual, so
-    # the FP32 operator only slows the contraction) with the loosest tolerance
-    # of the ladder that gets there; double-float sweeps reported beside.
-    def to_accuracy(form, refine_dtype=REFINE_DTYPE):
-        dt, fm, pc = FORMS[form]
-        err = None
-        for t in TOL_LADDER:
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if dt == "f64":
-                set_scaling(pc)
-                r = h.lsqr(d, p.w, p.lam, 100000, t, dtype=dt, fmt=fm, precond=1 if pc else 0)
+    # ---- the plain FP64 form at the same accuracy, with its own roofline
+    plain_roof = kernel_roofline(S, PLAIN, peak)
+    chosen_roof = kernel_roofline(S, args.form, peak)
+    accuracy = {"target_model_error": ACC_TARGET, "reference": ref_desc,
+                "chosen": {"form": args.form, "s": ms / 1e3, "iters": res.info["iters"],
+                           "sweeps": res.info["sweeps"], "model_error": headline_err,
+                           "calibration": cal}}
+    if headline_acc:
+        pcal = calibrate(S, PLAIN, relerr, stream)
+        if pcal["tol"] is not None:
+            ms_p, res_p, _ = timed(PLAIN, 2, 0, **S.acc_kw(PLAIN, pcal["tol"]))
+            accuracy["plain_fp64"] = {"form": PLAIN, "tol": pcal["tol"], "s": ms_p / 1e3,
+                                      "iters": res_p.info["iters"],
+                                      "model_error": relerr(res_p.m),
+                                      "kernels": plain_roof}
+            accuracy["speedup_vs_plain_fp64"] = ms_p / ms
+        else:
+            accuracy["plain_fp64"] = {"form": PLAIN, "tol": None, "calibration": pcal,
+                                      "kernels": plain_roof}
+        # the other scaling forms at the same target, for comparison
+        for other in ("f32-blocked-colnorm", "f32-blocked-learned"):
+            if other == args.form or (other.endswith("learned") and params is None):
+                continue
+            oc = calibrate(S, other, relerr, stream)
+            if oc["tol"] is not None:
+                ms_o, res_o, _ = timed(other, 2, 0, **S.acc_kw(other, oc["tol"]))
+                accuracy[other] = {"s": ms_o / 1e3, "tol": oc["tol"],
+                                   "iters": res_o.info["iters"], "model_error": relerr(res_o.m)}
             else:
-                set_scaling(pc)
-                r = h.lsqr(d, p.w, p.lam, 100000, p.tol, dtype=dt, fmt=fm,
-                           precond=1 if pc else 0, refine=3, refine_dtype=refine_dtype,
-                           refine_tol=t)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            err = relerr(r.m)
-            if err <= ACC_TARGET:
-                if dt != "f64":
-                    return {"refine_tol": t, "refine_dtype": refine_dtype,
-                            "s": e0.elapsed_time(e1) / 1e3, "iters": r.info["iters"],
-                            "sweeps": r.info["sweeps"], "model_error": err}
-                return {"tol": t,
-                        "s": e0.elapsed_time(e1) / 1e3, "iters": r.info["iters"],
-                        "sweeps": r.info["sweeps"], "model_error": err}
-        return {"s": None, "iters": None, "model_error": err}
+                accuracy[other] = {"s": None, "calibration": oc}
 
-    if args.no_accuracy:
-        accuracy_matched = None
-    else:
-        acc_chosen = to_accuracy(args.form)
-        acc_plain = to_accuracy(PLAIN)
-        accuracy_matched = {"target_model_error": ACC_TARGET, "chosen": acc_chosen,
-                            "plain_fp64": acc_plain,
-                            "speedup": (acc_plain["s"] / acc_chosen["s"])
-                            if acc_plain["s"] and acc_chosen["s"] else None}
-        # the column-norm form as well: the learned scaling is trained for the
-        # FP32 solve, not for the refinement sweeps
-        if args.form != "f32-blocked-colnorm":
-            acc_cn = to_accuracy("f32-blocked-colnorm")
-            accuracy_matched["f32-blocked-colnorm"] = acc_cn
-            if acc_plain["s"] and acc_cn["s"]:
-                accuracy_matched["speedup_colnorm"] = acc_plain["s"] / acc_cn["s"]
-        # the same two-phase solve with double-float refinement sweeps
-        acc_df = to_accuracy(args.form, "df64")
-        accuracy_matched["df64_refinement"] = acc_df
-        if acc_plain["s"] and acc_df["s"]:
-            accuracy_matched["speedup_df64_refinement"] = acc_plain["s"] / acc_df["s"]
+    # ---- time to the workload's tolerance (one solve), chosen and plain
+    ms_c6, res_c6, _ = timed(args.form, max(1, min(args.steps, 3)), 1)
+    ms_p6, res_p6, _ = timed(PLAIN, max(1, min(args.steps, 3)), 1)
+    tol_sec = {"tol": p.tol,
+               "chosen": {"s": ms_c6 / 1e3, "iters": res_c6.info["iters"],
+                          "istop": res_c6.info["istop"], "model_error": relerr(res_c6.m)},
+               "plain_fp64": {"s": ms_p6 / 1e3, "iters": res_p6.info["iters"],
+                              "model_error": relerr(res_p6.m), "kernels": plain_roof},
+               "speedup_vs_plain_fp64": ms_p6 / ms_c6}
 
-    # LSMR (the paper's solver) on the same sweeps: chosen form and plain FP64
+    # ---- LSMR (the paper's solver) on the same sweeps: chosen form and plain FP64
     lsmr_sec = None
     if not args.no_lsmr:
         ms_l, res_l, _ = timed(args.form, max(1, min(args.steps, 3)), 1, method="lsmr")
         ms_lp, res_lp, _ = timed(PLAIN, 1, 1, method="lsmr")
-        lsmr_sec = {"chosen": {"s": ms_l / 1e3, "iters": res_l.info["iters"],
-                               "istop": res_l.info["istop"],
-                               "model_error_vs_fp64_ref": relerr(res_l.m)},
+        lsmr_sec = {"tol": p.tol,
+                    "chosen": {"s": ms_l / 1e3, "iters": res_l.info["iters"],
+                               "istop": res_l.info["istop"], "model_error": relerr(res_l.m)},
                     "plain_fp64": {"s": ms_lp / 1e3, "iters": res_lp.info["iters"],
-                                   "model_error_vs_fp64_ref": relerr(res_lp.m)},
+                                   "model_error": relerr(res_lp.m), "kernels": plain_roof},
                     "speedup_vs_plain_fp64": ms_lp / ms_l}
 
-    # damping sweep: 8 damping values from one bidiagonalisation vs 8 solves
+    # ---- damping sweep: 8 damping values from one bidiagonalisation vs 8 solves
     sweep_sec = None
     if not args.no_sweep:
         lams = [float(10.0 ** (-3 + 3 * i / 7)) for i in range(8)]   # logspace(-3, 0, 8)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sw = h.lsqr_damping_sweep(d, p.w, lams, itmax, p.tol, dtype="f32", fmt="blocked")
-        torch.cuda.synchronize()
-        t_sweep = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        sep = [h.lsqr(d, p.w, lm, itmax, p.tol, dtype="f32", fmt="blocked") for lm in lams]
-        torch.cuda.synchronize()
-        t_sep = time.perf_counter() - t0
+        t_sweep, sw = event_time(stream, lambda: h.lsqr_damping_sweep(
+            S.d, p.w, lams, p.itmax, p.tol, dtype="f32", fmt="blocked"))
+        t_sep, sep = event_time(stream, lambda: [
+            h.lsqr(S.d, p.w, lm, p.itmax, p.tol, dtype="f32", fmt="blocked") for lm in lams])
         sweep_sec = {"lambdas": lams, "form": "f32-blocked (no scaling)",
                      "sweep_s": t_sweep, "separate_s": t_sep, "speedup": t_sep / t_sweep,
                      "iters": [r.info["iters"] for r in sw],
                      "identical_to_separate": all(
                          bool(torch.equal(a.m, b.m)) for a, b in zip(sw, sep))}
 
-    # per-kernel device time (events around each launch, same solve)
-    prof = solve(args.form, profile=True)
-    pi = max(prof.info["profiled_iters"], 1)
-    kms = {"fwd": prof.info["fwd_ms"] / pi, "adj": prof.info["adj_ms"] / pi,
-           "upd": prof.info["upd_ms"] / pi}
-    ab = algorithmic_bytes(h, p, dtype, fmt, precond > 0)
+    # ---- roofline of the dominant sweep of the chosen form
+    kms = chosen_roof["kernel_ms_per_iter"]
     dom = max(("fwd", "adj"), key=lambda k: kms[k])
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
-    peak = peaks.get("hbm_gbs", 6400.0)
-    achieved = ab[dom] / (kms[dom] * 1e-3) / 1e9
     kernel_name = {"fwd": "k_fwd", "adj": "k_adj"}[dom]
+    ab = chosen_roof["bytes"]
+    achieved = ab[dom] / (kms[dom] * 1e-3) / 1e9
     out["roofline"] = {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1),
                        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                        "traffic": dram_traffic_record(kernel_name, args.form, args.workload),
-                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
-                       if "hbm_gbs" in peaks else "fallback 6400 GB/s",
-                       "algorithmic_bytes_per_launch": ab[dom],
-                       "avg_launch_ms": round(kms[dom], 5)}
-    spmv_gbs = {k: round(ab[k] / (kms[k] * 1e-3) / 1e9, 1) for k in ("fwd", "adj")}
+                       "peak_source": peak_src, "algorithmic_bytes_per_launch": ab[dom],
+                       "avg_launch_ms": kms[dom], "other_sweep": {
+                           "kernel": {"fwd": "k_adj", "adj": "k_fwd"}[dom],
+                           "frac": chosen_roof["frac_of_hbm"]["adj" if dom == "fwd" else "fwd"]}}
 
-    # end to end through the host entry point (pinned host d and m)
+    # ---- end to end through the host entry point (pinned host d and m)
     e2e = None
     if not args.no_e2e:
         dh = torch.empty(h.m, dtype=torch.float64, pin_memory=True)
-        dh.copy_(d.cpu())
+        dh.copy_(S.d.cpu())
         mh = torch.empty(h.n, dtype=torch.float64, pin_memory=True)
         dn, mn = dh.numpy(), mh.numpy()
         dt_, fm_, pc_ = FORMS[args.form]
-        set_scaling(pc_)
-        h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_, precond=min(pc_, 1))
+        hkw = dict(kw)
+        itmax_h = hkw.pop("itmax", p.itmax)
+        tol_h = hkw.pop("tol", p.tol)
+
+        def host_step():
+            S.set_scaling(pc_)
+            h.lsqr_host(dn, p.w, p.lam, itmax_h, tol_h, m_out=mn, dtype=dt_, fmt=fm_,
+                        precond=min(pc_, 1), **hkw)
+        host_step()
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            set_scaling(pc_)
-            h.lsqr_host(dn, p.w, p.lam, itmax, p.tol, m_out=mn, dtype=dt_, fmt=fm_,
-                        precond=min(pc_, 1))
+            host_step()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * h.m,
-               "d2h_bytes_per_step": 8 * h.n}
+               "d2h_bytes_per_step": 8 * h.n,
+               "model_error": relerr(torch.from_numpy(mn.copy()).cuda())}
 
     out.update({
-        "reference": {"form": PLAIN, "tol": args.ref_tol, "iters": ref.info["iters"],
-                      "istop": ref.info["istop"]},
-        "config": {"workload": workload_desc(p), "form": args.form,
+        "config": {"workload": workload_desc(p), "form": args.form, "metric_kind": metric_kind,
                    "plain_form": PLAIN, "nnz": h.nnz,
                    "l2_policy": "inputs larger than L2 (G values+indices "
                                 f"{(VALUE_BYTES[dtype] * 2 * h.nnz) / 1e9:.2f} GB > 126 MB)",
-                   "step": "one LSQR solve to tol on device-resident G (graph replay)",
+                   "step": step_desc, "reference": ref_desc["source"],
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
-        "iters": it_chosen,
+        "iters": res.info["iters"],
         "istop": res.info["istop"],
-        "model_error_vs_fp64_ref": relerr(m_chosen),
-        "plain_fp64": {"s": ms_plain / 1e3, "iters": res_plain.info["iters"],
-                       "model_error_vs_fp64_ref": relerr(m_plain)},
-        "speedup_vs_plain_fp64": ms_plain / ms,
-        "accuracy_matched": accuracy_matched,
+        "model_error_vs_reference": headline_err,
+        "accuracy_matched": accuracy,
+        "time_to_tol": tol_sec,
         "lsmr": lsmr_sec,
         "damping_sweep": sweep_sec,
-        "kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
-        "spmv_gbs": spmv_gbs,
-        "build_G_s": build_s,
-        "iters_per_s": it_chosen / (ms / 1e3),
+        "kernels": chosen_roof,
+        "build_G_s": S.build_s,
+        "iters_per_s": res.info["iters"] / (ms / 1e3),
     })
-
-    h.close()
+    S.close()
     if not args.no_batched:
         out["batched"] = batched_section(args.batched_systems)
+    if not args.no_extra_workloads and args.workload == "mid":
+        out["workloads"] = {w: workload_section(w, args.form, params, peak, stream)
+                            for w in ("paper", "large")}
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(p, args.cpu_sample_iters, res_plain.info["iters"])
+        out["cpu_baseline"] = cpu_baseline(p, args.workload, args.cpu_sample_iters, metric_kind)
     if rank == 0:
         print(json.dumps(out))
 
 
-def batched_section(nsys=64, steps=2):
+def workload_section(name, form, params, peak, stream, steps=2):
+    """Compact record of another workload in the default run: one warm-up and
+    `steps` timed solves to the workload's tol of the chosen form and of the
+    plain FP64 form, the per-kernel roofline of both, and the model error
+    against the oracle's stored solution where there is one (the
+    paper-shaped system), else against a GPU FP64 solve (100 x 100 x 20:
+    its oracle checks, on sampled rows and true residual norms, are in the
+    full-size tests).  Only the value copies the section uses are built."""
+    import torch
+    p = make_problem(name, 0)
+    S = System(p, {"f64", "f32"}, params=params)
+    m_ref_np, meta = load_mref(name, p.seed)
+
+    def solve_t(f, **kw):
+        times, r = [], None
+        S.solve(f, **kw)
+        for _ in range(steps):
+            s, r = event_time(stream, lambda: S.solve(f, **kw))
+            times.append(s)
+        return statistics.mean(times), r
+
+    s_c, r_c = solve_t(form)
+    s_p, r_p = solve_t(PLAIN)
+    if m_ref_np is not None:
+        relerr = relerr_to(torch.from_numpy(m_ref_np).cuda())
+        ref = {"source": "FP64 CPU oracle (stored, tests/golden)", "tol": meta["atol"]}
+    else:
+        relerr = relerr_to(r_p.m)
+        ref = {"source": f"GPU plain FP64 solve at the same tol {p.tol:g} (not the oracle)"}
+    sec = {"workload": workload_desc(p), "nnz": S.h.nnz, "build_G_s": S.build_s,
+           "reference": ref,
+           "time_to_tol": {"tol": p.tol,
+                           "chosen": {"form": form, "s": s_c, "iters": r_c.info["iters"],
+                                      "model_error": relerr(r_c.m)},
+                           "plain_fp64": {"s": s_p, "iters": r_p.info["iters"],
+                                          "model_error": relerr(r_p.m)},
+                           "speedup_vs_plain_fp64": s_p / s_c},
+           "kernels": {"chosen": kernel_roofline(S, form, peak),
+                       "plain_fp64": kernel_roofline(S, PLAIN, peak)}}
+    for k in ("chosen", "plain_fp64"):
+        sec["kernels"][k].pop("bytes", None)
+    if m_ref_np is not None:
+        acc = {}
+        for key, f in (("chosen", form), ("plain_fp64", PLAIN)):
+            c = calibrate(S, f, relerr, stream)
+            if c["tol"] is not None:
+                s, r = solve_t(f, **S.acc_kw(f, c["tol"]))
+                acc[key] = {"s": s, "tol": c["tol"], "iters": r.info["iters"],
+                            "model_error": relerr(r.m)}
+            else:
+                acc[key] = {"s": None, "calibration": c}
+        if acc["chosen"]["s"] and acc["plain_fp64"]["s"]:
+            acc["speedup_vs_plain_fp64"] = acc["plain_fp64"]["s"] / acc["chosen"]["s"]
+        sec["accuracy_matched"] = acc
+    S.close()
+    return sec
+
+
+def batched_section(nsys=64, steps=2, itmax=3000, sample_every=4):
     """The batched workload: nsys uneven systems (grids 24x24x8 .. 64x64x16),
     16 right-hand sides each sharing G (8 checkerboards at the system's
-    lambda, the blob model at 8 damping values 1e-3..1), FP32 values, tol 1e-6,
-    solved by pdst_lsqr_batched.  Compared with one-at-a-time FP32 solves of the
-    same pairs on a sample of systems, scaled by stored entries x pairs."""
+    lambda, the blob model at 8 damping values 1e-3..1), FP32 values, FP64
+    scalars, column-norm scaling per system (lambda_j D rows per pair), tol
+    1e-6, solved by pdst_lsqr_batched.  Compared with one-at-a-time solves of
+    the same pairs in the same form (same D, same lambda_j rows), all 16 pairs
+    of every `sample_every`-th system measured, scaled to the batch by stored
+    entries x iterations."""
     import numpy as np
     import torch
 
@@ -532,101 +695,152 @@ def batched_section(nsys=64, steps=2):
             cols.append(gm + p.noise_frac * rms * z)
         ds.append(torch.stack(cols, dim=1).contiguous())
         lams.append([lam for _, lam in synth.batched_rhs_models(p)])
+        h.set_col_scaling(None, p.w, p.lam)      # column norms with the system's lambda
         hs.append(h)
     w = [p.w for p in ps]
     nnz = [h.nnz for h in hs]
-    outs, infos, opts = pdst.lsqr_batched(hs, ds, w, lams, 2000, 1e-6, dtype="f32")  # + tune
+    outs, infos, opts = pdst.lsqr_batched(hs, ds, w, lams, itmax, 1e-6, dtype="f32",
+                                          precond=1)   # + autotune
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        outs, infos, opts2 = pdst.lsqr_batched(hs, ds, w, lams, 2000, 1e-6, dtype="f32")
+        outs, infos, opts2 = pdst.lsqr_batched(hs, ds, w, lams, itmax, 1e-6, dtype="f32",
+                                               precond=1)
     torch.cuda.synchronize()
     t_batch = (time.perf_counter() - t0) / steps
     iters = [inf["iters"] for row in infos for inf in row]
-    conv = sum(inf["istop"] in (1, 2) for row in infos for inf in row)
-    # one-at-a-time reference on a sample of systems (largest, median, smallest)
-    order = np.argsort(nnz)
-    sample = sorted({int(order[-1]), int(order[len(order) // 2]), int(order[0])})
-    t_single, work_single = 0.0, 0
+    conv = [inf["istop"] in (1, 2) for row in infos for inf in row]
+    recipe_names = [f"checkerboard b={b}" for b in (2, 3, 4, 5, 6, 7, 8)] + ["-checkerboard b=8"]
+    recipe_names += [f"blobs lambda={l:.3g}" for l in np.logspace(-3.0, 0.0, 8)]
+    per_recipe = {nm: {"converged": int(sum(infos[s][j]["istop"] in (1, 2) for s in range(nsys))),
+                       "iters_mean": float(np.mean([infos[s][j]["iters"] for s in range(nsys)]))}
+                  for j, nm in enumerate(recipe_names)}
+    # one-at-a-time solves of every pair of the sampled systems, measured
+    sample = list(range(0, nsys, sample_every))
+    t_single, work_single, it_single = 0.0, 0, 0
     for s in sample:
         for j in range(ds[s].shape[1]):
             dj = ds[s][:, j].contiguous()
-            hs[s].lsqr(dj, w[s], lams[s][j], 2000, 1e-6, dtype="f32", fmt="blocked")
+            hs[s].lsqr(dj, w[s], lams[s][j], itmax, 1e-6, dtype="f32", fmt="blocked", precond=1)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            hs[s].lsqr(dj, w[s], lams[s][j], 2000, 1e-6, dtype="f32", fmt="blocked")
+            r = hs[s].lsqr(dj, w[s], lams[s][j], itmax, 1e-6, dtype="f32", fmt="blocked",
+                           precond=1)
             torch.cuda.synchronize()
             t_single += time.perf_counter() - t1
-        work_single += nnz[s] * ds[s].shape[1]
-    total_work = sum(n * d.shape[1] for n, d in zip(nnz, ds))
+            work_single += nnz[s] * r.info["iters"]
+            it_single += r.info["iters"]
+    total_work = sum(nnz[s] * infos[s][j]["iters"] for s in range(nsys)
+                     for j in range(ds[s].shape[1]))
     t_seq_est = t_single * total_work / work_single
+    total_nnz_iters = total_work
     for h in hs:
         h.close()
     return {"workload": f"{nsys} systems (grids 24x24x8..64x64x16), 16 right-hand sides each, "
-                        "FP32 values, tol 1e-6",
-            "total_nnz": int(sum(nnz)), "pairs": len(iters), "converged_pairs": conv,
+                        "FP32 values, FP64 scalars, column-norm scaling per system, tol 1e-6, "
+                        f"itmax {itmax}",
+            "total_nnz": int(sum(nnz)), "pairs": len(iters), "converged_pairs": int(sum(conv)),
+            "per_recipe": per_recipe,
             "batch_s": t_batch, "solves_per_s": len(iters) / t_batch,
             "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
-            "chosen_tile_rows": opts["chosen_tile_rows"], "autotune_fwd_ms": opts["tune_ms"][:3],
+            "entries_x_iters_per_s": total_nnz_iters / t_batch,
+            "chosen_tile_rows": opts["chosen_tile_rows"], "autotune_iter_ms": opts["tune_ms"][:3],
             "gpu_launches": opts2["kernel_launches"],
-            "one_at_a_time_estimate_s": t_seq_est,
-            "speedup_vs_one_at_a_time": t_seq_est / t_batch,
-            "one_at_a_time_sample": f"systems {sample} ({sum(ds[s].shape[1] for s in sample)} "
-                                    "single solves), scaled by stored entries x right-hand sides"}
+            "one_at_a_time": {"measured_s": t_single, "solves": len(sample) * 16,
+                              "systems": sample, "iters": it_single,
+                              "scaled_to_batch_s": t_seq_est,
+                              "scaling": "measured time x (batch stored entries x iterations) / "
+                                         "(sample stored entries x iterations)"},
+            "speedup_vs_one_at_a_time": t_seq_est / t_batch}
 
 
-def cpu_baseline(p, sample_iters, iters_to_tol):
-    """FP64 CPU oracle on this machine's cores: a bounded sample of LSQR
-    iterations on the same system, scaled to the FP64 iteration count."""
+def oracle_iters_to_target(workload, seed):
+    """Iterations the oracle itself needs to come within ACC_TARGET of its
+    converged solution: the loosest rung of its stored ladder (one oracle run,
+    tests/golden) that gets there, with that rung; (None, None) if unknown."""
+    _, meta = load_mref(workload, seed)
+    if not meta:
+        return None, None
+    for rung in meta.get("ladder", []):
+        if rung["iters"] > 0 and rung["model_error"] <= ACC_TARGET:
+            return rung["iters"], rung
+    return None, None
+
+
+def time_oracle_iters(p, sample_iters, repeats=1, warmup=0):
+    """Seconds per FP64 oracle LSQR iteration on this machine's cores: the
+    mean over `repeats` bounded samples of `sample_iters` iterations."""
     import oracle
     oracle.build()
-    G = oracle.build_G_problem(p)
-    GT = oracle.transpose(G)
-    d = oracle.rhs_for(p, G)
-    t0 = time.perf_counter()
-    r = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0,
-                    itmax=sample_iters)
-    t = time.perf_counter() - t0
-    per_it = t / max(r.itn, 1)
-    return {"value": per_it * iters_to_tol, "unit": "s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{r.itn} FP64 oracle LSQR iterations on the same system in {t:.2f} s, "
-                      f"scaled to the {iters_to_tol} iterations the FP64 solve needs to reach tol",
-            "s_per_iter": per_it}
-
-
-def run_reference(args, rank, world):
-    """The FP64 CPU oracle as it stands, timed on the host cores."""
-    if rank != 0:
-        return
-    import oracle
-    oracle.build()
-    p = make_problem(args.workload, 0)
     G = oracle.build_G_problem(p)
     GT = oracle.transpose(G)
     d = oracle.rhs_for(p, G)
     grid = (p.nx, p.ny, p.nz)
-    # iteration count to tolerance of the oracle itself (untimed, once)
-    full = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=p.tol, btol=p.tol, itmax=p.itmax)
-    sample = args.cpu_sample_iters
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0, itmax=3)
     times = []
-    for _ in range(args.steps):
+    for _ in range(repeats):
         t0 = time.perf_counter()
-        r = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0, itmax=sample)
-        times.append((time.perf_counter() - t0) / r.itn)
-    per_it = statistics.mean(times)
-    value = per_it * full.itn
-    cb = {"value": value, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
-          "sample": f"{sample} FP64 oracle LSQR iterations per step, scaled to the oracle's "
-                    f"own {full.itn} iterations to tol"}
+        r = oracle.lsqr(G, GT, grid, p.w, p.lam, d, atol=0.0, btol=0.0, conlim=0.0,
+                        itmax=sample_iters)
+        times.append((time.perf_counter() - t0) / max(r.itn, 1))
+    return statistics.mean(times), oracle.num_threads(), (G, GT, d)
+
+
+def oracle_value(p, workload, per_it, system, metric_kind):
+    """The oracle's time on the benchmark's metric: seconds per iteration x the
+    iterations the oracle needs (to within ACC_TARGET of its solution for the
+    accuracy-matched metric, else to the workload's tol, found by one untimed
+    oracle solve)."""
+    if metric_kind == "time_to_1e-4":
+        its, rung = oracle_iters_to_target(workload, p.seed)
+        if its is not None:
+            return per_it * its, (f"the {its} iterations the oracle needs to come within "
+                                  f"{ACC_TARGET:g} of its converged solution (its stopping "
+                                  f"rule at tol {rung['tol']:g}; stored ladder)")
+    import oracle
+    G, GT, d = system
+    full = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, p.lam, d, atol=p.tol, btol=p.tol,
+                       itmax=p.itmax)
+    return per_it * full.itn, f"the oracle's own {full.itn} iterations to tol {p.tol:g}"
+
+
+def cpu_baseline(p, workload, sample_iters, metric_kind):
+    """FP64 CPU oracle on this machine's cores: a bounded sample of LSQR
+    iterations on the same system, scaled to the iterations the oracle needs
+    for the benchmark's metric."""
+    per_it, cores, system = time_oracle_iters(p, sample_iters)
+    value, what = oracle_value(p, workload, per_it, system, metric_kind)
+    return {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample_iters} FP64 oracle LSQR iterations on the same system "
+                      f"({per_it * 1e3:.1f} ms each), scaled to {what}",
+            "s_per_iter": per_it}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, timed on the host cores, on the
+    benchmark's metric: each step a bounded sample of oracle iterations,
+    scaled to the iterations the oracle needs."""
+    if rank != 0:
+        return
+    p = make_problem(args.workload, 0)
+    metric_kind = ("time_to_1e-4" if not args.no_accuracy and
+                   oracle_iters_to_target(args.workload, p.seed)[0] else
+                   f"time_to_tol_{p.tol:g}")
+    sample = args.cpu_sample_iters
+    per_it, cores, system = time_oracle_iters(p, sample, repeats=args.steps,
+                                              warmup=args.warmup)
+    value, what = oracle_value(p, args.workload, per_it, system, metric_kind)
+    cb = {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+          "sample": f"{sample} FP64 oracle LSQR iterations per step ({per_it * 1e3:.1f} ms "
+                    f"each), scaled to {what}"}
     print(json.dumps({"metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": per_it * sample * 1e3, "higher_is_better": False,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic (seeded generator; no dataset)",
-                      "config": {"workload": workload_desc(p), "form": "oracle-f64"},
+                      "config": {"workload": workload_desc(p), "form": "oracle-f64",
+                                 "metric_kind": metric_kind},
                       "impl": "reference", "cpu_baseline": cb,
                       "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}))

@@ -10,7 +10,7 @@ rows -- against the FP64 CPU oracle built from the same seeded inputs:
   by element, with the oracle's G, G^T and d (bars: 1e-10 for FP64 values,
   1e-9 double-float, 1e-4 FP32, 3e-2 BF16, unscaled and column-scaled);
 * the converged solutions against the oracle's own tol-1e-12 solution stored
-  in tests/golden/mid_mref.npy (written by tests/golden/make_mid_mref.py,
+  in tests/golden/mid_mref.npy (written by tests/golden/make_mref.py,
   which calls only the oracle): the plain FP64 form and the two-phase FP32
   form, the benchmark's accuracy-matched path, within 1e-4 relative model
   error, and the relative residual difference within 1e-6.
