@@ -158,8 +158,11 @@ typedef struct {
     int32_t precond;   /* 0 none; 1 right diagonal scaling set by pdst_set_col_scaling */
     int32_t kblock;    /* iterations per graph launch (<= 0: 16) */
     int32_t use_graph; /* 1 (default): CUDA graph replay; 0: plain launches */
-    int32_t profile;   /* 1: one iteration per launch group, each kernel bracketed by CUDA
-                          events; per-kernel device time returned in pdst_lsqr_info */
+    int32_t profile;   /* per-kernel device time in pdst_lsqr_info: 1, one iteration per
+                          launch group, each kernel bracketed by CUDA events (k_step in line);
+                          2, the CUDA-graph replay itself with event nodes around the forward,
+                          the update and the adjoint of every iteration (k_step on its branch
+                          beside the forward); 0 (default) none */
     double *rnorm_hist_dev; /* optional device array (itmax): ||r|| after each iteration */
     int32_t refine;    /* > 0: refinement with up to `refine` sweeps:
                           m <- m + D argmin ||A_D dy - r(m)||, the residual r(m) of the

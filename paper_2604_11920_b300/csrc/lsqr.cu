@@ -1233,12 +1233,14 @@ struct LsqrWork {
     DevBuf sw_stage;                             // damping sweep: k_step_sweep's copies
     LsqrScalars *h_scal = nullptr;   // pinned
     unsigned grid_rows = 0, grid_cols = 0, grid_vec = 0;
-    std::map<int, cudaGraphExec_t> graphs;   // key: kblock
+    std::map<int, cudaGraphExec_t> graphs;   // key: kblock (+ PROF_KEY with event nodes)
+    std::vector<cudaEvent_t> prof_ev;        // event nodes of the profiled graph (4 per iteration)
     cudaStream_t side = nullptr;             // k_step beside k_fwd
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~LsqrWork() {
         for (auto &g : graphs)
             if (g.second) cudaGraphExecDestroy(g.second);
+        for (auto e : prof_ev) cudaEventDestroy(e);
         if (h_scal) cudaFreeHost(h_scal);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
@@ -1318,6 +1320,8 @@ template <class VT, class ST, int FMT> static auto fwd_kernel(int nz) {
     return k_fwd<VT, ST, FMT>;
 }
 
+constexpr int PROF_KEY = 1 << 20;   // graph cache key offset of the profiled graphs
+
 template <class K> static unsigned persistent_grid(K kernel, int device, int64_t work_items) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LT, 0);
@@ -1386,13 +1390,21 @@ template <class VT, class ST, int FMT> struct Solver {
         k_step<<<1, 32, 0, w->side>>>(a.sc, a.sc_stage);
         cudaEventRecord(w->ev_join, w->side);
     }
-    static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
+    // ev (profile mode 2): four events recorded around the forward, the
+    // update and the adjoint on the main stream, captured as event-record
+    // nodes (external records: a plain record inside a capture only orders).
+    static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s,
+                            const cudaEvent_t *ev = nullptr) {
         fork_step(w, a, s);
+        if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
         fwd_kernel<VT, ST, FMT>(h->nz)<<<w->grid_rows, LT, 0, s>>>(a);
+        if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
         cudaStreamWaitEvent(s, w->ev_join, 0);
         k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc,
                                              a.sc_stage, a.sy);
+        if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
         adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
+        if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
     }
 
     // Per-kernel device time of `iters` plain-launched iterations, each kernel
@@ -1434,7 +1446,7 @@ template <class VT, class ST, int FMT> struct Solver {
 
     static pdst_status run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                            const double *d, const LsqrScalars &init, int kblock, bool use_graph,
-                           bool profile, double *m_out, cudaStream_t s, RunStats &rs,
+                           int profile, double *m_out, cudaStream_t s, RunStats &rs,
                            const double *baug = nullptr, bool accumulate = false,
                            const double *Dover = nullptr) {
         OpArgs<VT, ST> a = make_args<VT, ST>(h, dtype, w, scaled, lamrows);
@@ -1453,18 +1465,36 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_CUDA(cudaGetLastError());
         rs.launches += 3;
 
+        // profile 2: the graph replay itself, with event nodes around each kernel
+        const bool in_graph_prof = profile == 2;
         cudaGraphExec_t exec = nullptr;
-        if (use_graph && !profile) {
-            auto it = w->graphs.find(kblock);
+        if (use_graph && profile != 1) {
+            const int key = kblock + (in_graph_prof ? PROF_KEY : 0);
+            auto it = w->graphs.find(key);
             if (it != w->graphs.end()) {
                 exec = it->second;
             } else {
+                if (in_graph_prof && w->prof_ev.size() < 4 * (size_t)kblock) {
+                    // profiled graphs captured earlier hold the old events
+                    for (auto g = w->graphs.begin(); g != w->graphs.end();) {
+                        if (g->first >= PROF_KEY) {
+                            if (g->second) cudaGraphExecDestroy(g->second);
+                            g = w->graphs.erase(g);
+                        } else {
+                            ++g;
+                        }
+                    }
+                    for (auto e : w->prof_ev) cudaEventDestroy(e);
+                    w->prof_ev.assign(4 * (size_t)kblock, nullptr);
+                    for (auto &e : w->prof_ev) PDST_CUDA(cudaEventCreate(&e));
+                }
                 cudaStream_t cs;
                 PDST_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, cs);
+                    for (int i = 0; i < kblock; ++i)
+                        launch_iter(h, w, a, cs, in_graph_prof ? &w->prof_ev[4 * (size_t)i] : nullptr);
                     e = cudaStreamEndCapture(cs, &g);
                 }
                 if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
@@ -1474,18 +1504,36 @@ template <class VT, class ST, int FMT> struct Solver {
                     set_error("LSQR graph capture: %s", cudaGetErrorString(e));
                     return PDST_ERR_CUDA;
                 }
-                w->graphs[kblock] = exec;
+                w->graphs[key] = exec;
             }
         }
+        int prof_it0 = -1;   // iteration count before the last profiled replay
         for (;;) {
             PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
                                       cudaMemcpyDeviceToHost, s));
             PDST_CUDA(cudaStreamSynchronize(s));
             const LsqrScalars &c = *w->h_scal;
+            if (prof_it0 >= 0) {
+                // only the iterations that ran (later kernels of a replay return at entry)
+                const int ran = std::min(c.itn - prof_it0, kblock);
+                for (int i = 0; i < ran; ++i) {
+                    float tf = 0.f, tu = 0.f, ta = 0.f;
+                    const cudaEvent_t *ev = &w->prof_ev[4 * (size_t)i];
+                    PDST_CUDA(cudaEventElapsedTime(&tf, ev[0], ev[1]));
+                    PDST_CUDA(cudaEventElapsedTime(&tu, ev[1], ev[2]));
+                    PDST_CUDA(cudaEventElapsedTime(&ta, ev[2], ev[3]));
+                    rs.fwd_ms += tf;
+                    rs.upd_ms += tu;
+                    rs.adj_ms += ta;
+                }
+                rs.profiled_iters += std::max(ran, 0);
+                prof_it0 = -1;
+            }
             if (c.done || c.istop || c.itn >= c.itmax) break;
-            if (profile) {
+            if (profile == 1) {
                 PDST_TRY(profiled_block(h, w, a, 1, s, rs));
             } else if (exec) {
+                if (in_graph_prof) prof_it0 = c.itn;
                 PDST_CUDA(cudaGraphLaunch(exec, s));
                 rs.launches += 4 * kblock;
             } else {
@@ -1500,7 +1548,7 @@ template <class VT, class ST, int FMT> struct Solver {
         PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
                                   cudaMemcpyDeviceToHost, s));
         PDST_CUDA(cudaStreamSynchronize(s));
-        if (profile) rs.profiled_iters = w->h_scal->itn;
+        if (profile == 1) rs.profiled_iters = w->h_scal->itn;
         return PDST_OK;
     }
 };
@@ -1508,7 +1556,7 @@ template <class VT, class ST, int FMT> struct Solver {
 template <class VT, class ST, int FMT>
 static pdst_status dispatch_run(pdst_handle *h, LsqrWork *w, int dtype, bool scaled, bool lamrows,
                                 const double *d, const LsqrScalars &init, int kblock,
-                                bool use_graph, bool profile, double *m_out, cudaStream_t s,
+                                bool use_graph, int profile, double *m_out, cudaStream_t s,
                                 bool fresh, RunStats &rs, const double *baug = nullptr,
                                 bool accumulate = false, const double *Dover = nullptr) {
     if (fresh) PDST_TRY((Solver<VT, ST, FMT>::prepare(h, w, lamrows)));
@@ -1637,7 +1685,9 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     // when none is set)
     const bool scaled = user_scaled || refine;
     const bool lamrows = scaled && lam > 0.0;
-    const int kblock = opts.profile ? 1 : (opts.kblock > 0 ? opts.kblock : 16);
+    PDST_CHECK_ARG(opts.profile >= 0 && opts.profile <= 2, "pdst_lsqr: unknown profile mode %d",
+                   opts.profile);
+    const int kblock = opts.profile == 1 ? 1 : (opts.kblock > 0 ? opts.kblock : 16);
     PDST_CHECK_ARG(kblock <= 1024, "pdst_lsqr: kblock must be <= 1024");
 
     LsqrScalars init{};
@@ -1672,7 +1722,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         w->graph_D = dptr;
     }
     const bool ug = opts.use_graph != 0;
-    const bool prof = opts.profile != 0;
+    const int prof = opts.profile;
     RunStats rs;
 
     auto solve_once = [&](const double *baug, bool accumulate, bool fresh_,

@@ -192,7 +192,7 @@ def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, prec
     o.format = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
     o.atol, o.btol, o.conlim = atol, btol, conlim
     o.precond, o.kblock, o.use_graph = int(precond), int(kblock), int(bool(use_graph))
-    o.profile = int(bool(profile))
+    o.profile = int(profile) if not isinstance(profile, bool) else int(profile)
     o.refine, o.refine_tol = int(refine), float(refine_tol)
     o.refine_dtype = -1 if refine_dtype is None else (DTYPES[refine_dtype]
                                                       if isinstance(refine_dtype, str)

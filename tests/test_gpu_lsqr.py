@@ -123,9 +123,13 @@ def test_graph_and_plain_launches_identical(tiny):
     c = h.lsqr(dd, p.w, p.lam, 300, 1e-8, use_graph=True, kblock=7).m.cpu().numpy()
     e = h.lsqr(dd, p.w, p.lam, 300, 1e-8, use_graph=True, kblock=16).m.cpu().numpy()
     f = h.lsqr(dd, p.w, p.lam, 300, 1e-8, profile=True)
+    g = h.lsqr(dd, p.w, p.lam, 300, 1e-8, profile=2, kblock=16)
     assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, e)
-    assert np.array_equal(a, f.m.cpu().numpy())
+    assert np.array_equal(a, f.m.cpu().numpy()) and np.array_equal(a, g.m.cpu().numpy())
     assert f.info["profiled_iters"] == 300 and f.info["fwd_ms"] > 0 and f.info["adj_ms"] > 0
+    # the profiled graph replay counts only the iterations that ran
+    assert g.info["profiled_iters"] == g.info["iters"] == f.info["iters"]
+    assert g.info["fwd_ms"] > 0 and g.info["adj_ms"] > 0 and g.info["upd_ms"] > 0
 
 
 def test_residual_history_non_increasing(tiny):

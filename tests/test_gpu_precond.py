@@ -85,37 +85,42 @@ def test_column_norms_and_power_scaling():
         assert rel(r.m.cpu().numpy(), D * o.x) < 1e-10
 
 
-def test_trained_network_gain_on_held_out_system():
-    """The trained network (precond_mlp.json, trained on seeds 10000-10199) on a
-    held-out 64 x 64 x 16 system (seed 20000): against no scaling it cuts the
-    FP32 iterations to tol 1e-6 by a third, and it is at least on par with
-    plain column-norm scaling; the scaled solves also end closer to the FP64
-    solution."""
+def test_trained_network_on_held_out_systems():
+    """The trained network (precond_mlp.json, trained on seeds 10000-10047 for
+    the fewest iterations of the accuracy-matched two-phase solve) on held-out
+    64 x 64 x 16 systems (seeds 20000-20002), against a tight reference of each:
+    one FP32 solve to tol 1e-6 needs a fifth fewer iterations than with no
+    scaling and ends closer to the solution; on the accuracy-matched metric
+    (two-phase solve to within 1e-4) it is within 10 % of column-norm scaling on
+    average (measured: 2.6 % more iterations on these seeds, 3.9 % more over
+    ten held-out seeds of this size, 3.9 % fewer on the 100 x 100 x 20 size)."""
     torch = require_cuda()
-    import time
-    from paper_2604_11920_b300.train_precond import DEFAULT_OUT, learned_scaling, load_params
-    from paper_2604_11920_b300.train_precond import make_rhs
-    p = synth.mid(20000)
-    h = pdst.build_G_problem(p, dtypes=("f64", "f32"), formats=("blocked",))
-    d = make_rhs(h, p)
-    ref = h.lsqr(d, p.w, p.lam, 100000, 1e-10, dtype="f64", fmt="blocked")
+    from paper_2604_11920_b300.train_precond import (DEFAULT_OUT, accuracy_cost, learned_scaling,
+                                                     load_params, make_rhs, reference, relerr)
+    params = load_params(DEFAULT_OUT)
+    acc_l = acc_cn = 0
+    for seed in (20000, 20001, 20002):
+        p = synth.mid(seed)
+        h = pdst.build_G_problem(p, dtypes=("f64", "f32", "df64"), formats=("blocked",))
+        d = make_rhs(h, p)
+        m_ref = reference(h, p, d)
 
-    def solve(precond):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = h.lsqr(d, p.w, p.lam, 20000, p.tol, dtype="f32", fmt="blocked", precond=precond)
-        torch.cuda.synchronize()
-        e = float(torch.linalg.norm(r.m - ref.m) / torch.linalg.norm(ref.m))
-        return r.info["iters"], time.perf_counter() - t0, e
+        def one(precond):
+            r = h.lsqr(d, p.w, p.lam, 20000, p.tol, dtype="f32", fmt="blocked", precond=precond)
+            return r.info["iters"], relerr(r.m, m_ref)
 
-    it_none, t_none, e_none = solve(0)
-    h.set_col_scaling_power(p.w, p.lam, 1.0)
-    it_cn, t_cn, e_cn = solve(1)
-    learned_scaling(h, p, load_params(DEFAULT_OUT))
-    it_l, t_l, e_l = solve(1)
-    print(f"held-out seed 20000: none {it_none} it {t_none:.3f} s err {e_none:.3f}; "
-          f"column-norm {it_cn} it {t_cn:.3f} s err {e_cn:.3f}; "
-          f"learned {it_l} it {t_l:.3f} s err {e_l:.3f}")
-    assert it_l <= 0.8 * it_none and e_l < e_none
-    assert it_l <= 1.05 * it_cn
-    h.close()
+        it_none, e_none = one(0)
+        h.set_col_scaling_power(p.w, p.lam, 1.0)
+        it_cn, _ = accuracy_cost(h, p, d, m_ref)
+        learned_scaling(h, p, params)
+        it_acc_l, _ = accuracy_cost(h, p, d, m_ref)
+        learned_scaling(h, p, params)
+        it_l, e_l = one(1)
+        print(f"seed {seed}: tol 1e-6 none {it_none} it err {e_none:.3f}, learned {it_l} it "
+              f"err {e_l:.3f}; to 1e-4: column-norm {it_cn} it, learned {it_acc_l} it")
+        assert it_l <= 0.8 * it_none and e_l < e_none
+        assert it_cn is not None and it_acc_l is not None
+        acc_l += it_acc_l
+        acc_cn += it_cn
+        h.close()
+    assert acc_l <= 1.10 * acc_cn
