@@ -407,7 +407,7 @@ def run_pdst(args, rank, world):
     if precond == 2 or os.path.exists(MODEL_PATH):
         from paper_2604_11920_b300.train_precond import load_params
         params = load_params(MODEL_PATH) if os.path.exists(MODEL_PATH) else None
-    S = System(p, {"f64", "df64", "f32", dtype}, params=params)
+    S = System(p, {"f64", "f32", "bf16", dtype}, params=params)
     h = S.h
 
     # ---- the reference solution: the oracle's, stored; else the GPU's FP64 solve
@@ -490,8 +490,9 @@ def run_pdst(args, rank, world):
         else:
             accuracy["plain_fp64"] = {"form": PLAIN, "tol": None, "calibration": pcal,
                                       "kernels": plain_roof}
-        # the other scaling forms at the same target, for comparison
-        for other in ("f32-blocked-colnorm", "f32-blocked-learned"):
+        # the other forms at the same target, for comparison: learned scaling,
+        # and BF16 values for the first solve (the refinement sweeps stay FP32)
+        for other in ("f32-blocked-colnorm", "f32-blocked-learned", "bf16-blocked-colnorm"):
             if other == args.form or (other.endswith("learned") and params is None):
                 continue
             oc = calibrate(S, other, relerr, stream)
@@ -675,7 +676,7 @@ def workload_section(name, form, params, peak, stream, steps=2):
     return sec
 
 
-def batched_section(nsys=64, steps=2, itmax=3000, sample_every=4):
+def batched_section(nsys=64, steps=2, itmax=6000, sample_every=4):
     """The batched workload: nsys uneven systems (grids 24x24x8 .. 64x64x16),
     16 right-hand sides each sharing G (8 checkerboards at the system's
     lambda, the blob model at 8 damping values 1e-3..1), FP32 values, FP64
