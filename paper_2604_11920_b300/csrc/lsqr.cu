@@ -3,7 +3,7 @@
 // the solver of the paper's least-squares module ("Solver for the
 // Large-scale Linear System"; the paper names LSQR beside LSMR).
 //
-// One iteration is four kernels:
+// One iteration is five kernels:
 //   k_step the FP64 scalar recurrence of the previous adjoint (rotations, norm
 //          estimates, stopping rules), one warp, run beside k_fwd, which needs
 //          only alpha and beta (on B300 the step's chain of dependent FP64
@@ -12,7 +12,9 @@
 //   k_fwd  u-bar <- A v - alpha u and beta = ||u-bar||   (G rows: warp per CSR
 //          row, gather of v; L rows: 7-point stencil, thread per column)
 //   k_upd  x += t1 w, w = v + t2 w in FP64 and ||w||^2 with the step's
-//          coefficients, which its last block publishes
+//          coefficients; after k_step on the same side branch, beside k_fwd
+//          (it reads v-bar and writes x, w, which the forward does not touch)
+//   k_pub  one block: publishes the step once both branches have joined
 //   k_adj  v-bar <- A^T u - beta v and alpha = ||v-bar|| (warp per CSC column,
 //          gather of u; the stencil term added by the same warp); its last
 //          block leaves the scalar step pending for the next k_step (the
@@ -1036,18 +1038,23 @@ __device__ __forceinline__ void publish_step(LsqrScalars *sc, const LsqrScalars 
 // LSMR (wv holds h): hbar = h - t1 hbar; x += t2 hbar; h = v - t3 h;  ||x||^2,
 // then the stopping tests on the new ||x|| (last block).  The coefficients
 // come from k_step's copy when a deferred step is pending; the last block
-// (block 0 when there is no update) then publishes it.
+// (block 0 when there is no update) then publishes it -- or, with defer = 1
+// (the update running on k_step's branch beside the forward, which still
+// writes beta), leaves its results in the copy for k_pub to publish.
 template <class ST>
 __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vbar, double *x,
                                             double *wv, double *hbar, double *partial,
-                                            LsqrScalars *sc, LsqrScalars *stage, LsqrSync *sy) {
+                                            LsqrScalars *sc, LsqrScalars *stage, LsqrSync *sy,
+                                            int defer = 0) {
     const bool pub = sc->step_pending != 0;
     const LsqrScalars *src = pub ? stage : sc;
     const int pend = src->pending;
     if (!pend) {
-        if (pub && blockIdx.x == 0) publish_step(sc, stage);
+        if (pub && !defer && blockIdx.x == 0) publish_step(sc, stage);
         return;
     }
+    // where the last block leaves the results: the copy when publishing later
+    LsqrScalars *dst = (pub && defer) ? stage : sc;
     const double alpha = src->alpha;
     const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
     const double t1 = src->t1, t2 = src->t2;
@@ -1073,11 +1080,11 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
         }
         double tot;
         if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot)) {
-            if (pub) publish_step(sc, stage);
+            if (pub && !defer) publish_step(sc, stage);
             if (threadIdx.x == 0) {
-                sc->xnorm = sqrt(tot);
-                if (pend != 2) stop_tests(sc);
-                sc->pending = 0;
+                dst->xnorm = sqrt(tot);
+                if (pend != 2) stop_tests(dst);
+                dst->pending = 0;
             }
         }
         return;
@@ -1092,13 +1099,21 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
     }
     double tot;
     if (grid_sum_last(ss, partial + 2 * MAXBLK, &sy->count[3], tot)) {
-        if (pub) publish_step(sc, stage);
+        if (pub && !defer) publish_step(sc, stage);
         if (threadIdx.x == 0) {
-            sc->wnorm2 = tot;
-            sc->pending = 0;
+            dst->wnorm2 = tot;
+            dst->pending = 0;
         }
     }
 }
+
+// Publication of the step that k_step and a deferred k_upd left in the copy
+// (one block, once both branches of the iteration have joined: the forward
+// wrote beta_{i+2} beside them).
+__global__ void __launch_bounds__(LT) k_pub(LsqrScalars *sc, const LsqrScalars *stage) {
+    if (sc->step_pending) publish_step(sc, stage);
+}
+
 
 // Damping sweep, y-slice l of the grid: x_l += t1 w_l; w_l = v + t2 w_l with
 // damping value l's coefficients (from k_step_sweep's copy when a step is
@@ -1380,14 +1395,28 @@ template <class VT, class ST, int FMT> struct Solver {
         return PDST_OK;
     }
 
-    // One iteration: the previous adjoint's scalar step (k_step, on a side
-    // stream) beside the forward, which needs only alpha_{i+1}; then the x/w
-    // update of that step (it reads v-bar_{i+1}, as the forward does); then
-    // the adjoint, which overwrites v-bar.
+    // One iteration: the previous adjoint's scalar step (k_step) and its x/w
+    // update (k_upd, which reads v-bar_{i+1}) on a side stream, beside the
+    // forward, which needs only alpha_{i+1}; then, once both branches are
+    // done, k_pub publishes the step and the adjoint overwrites v-bar.
+    // (Profile mode 1 and the allocation-free solve run the same kernels in
+    // line with k_upd publishing; the arithmetic, and so every bit, is the same.)
     static void fork_step(LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s) {
         cudaEventRecord(w->ev_fork, s);
         cudaStreamWaitEvent(w->side, w->ev_fork, 0);
         k_step<<<1, 32, 0, w->side>>>(a.sc, a.sc_stage);
+        cudaEventRecord(w->ev_join, w->side);
+    }
+    // The scalar step and then the x/w update on the side branch (the update
+    // reads v-bar and writes x and w, which the forward does not touch; it
+    // leaves its results in the step's copy), beside the forward.
+    static void fork_step_update(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a,
+                                 cudaStream_t s) {
+        cudaEventRecord(w->ev_fork, s);
+        cudaStreamWaitEvent(w->side, w->ev_fork, 0);
+        k_step<<<1, 32, 0, w->side>>>(a.sc, a.sc_stage);
+        k_upd<ST><<<w->grid_vec, LT, 0, w->side>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial,
+                                                   a.sc, a.sc_stage, a.sy, 1);
         cudaEventRecord(w->ev_join, w->side);
     }
     // ev (profile mode 2): four events recorded around the forward, the
@@ -1395,13 +1424,12 @@ template <class VT, class ST, int FMT> struct Solver {
     // nodes (external records: a plain record inside a capture only orders).
     static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s,
                             const cudaEvent_t *ev = nullptr) {
-        fork_step(w, a, s);
+        fork_step_update(h, w, a, s);
         if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
         fwd_kernel<VT, ST, FMT>(h->nz)<<<w->grid_rows, LT, 0, s>>>(a);
         if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
         cudaStreamWaitEvent(s, w->ev_join, 0);
-        k_upd<ST><<<w->grid_vec, LT, 0, s>>>(h->n, a.vbar, a.x, a.wv, a.hbar, a.partial, a.sc,
-                                             a.sc_stage, a.sy);
+        k_pub<<<1, LT, 0, s>>>(a.sc, a.sc_stage);
         if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
         adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
         if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
@@ -1535,11 +1563,11 @@ template <class VT, class ST, int FMT> struct Solver {
             } else if (exec) {
                 if (in_graph_prof) prof_it0 = c.itn;
                 PDST_CUDA(cudaGraphLaunch(exec, s));
-                rs.launches += 4 * kblock;
+                rs.launches += 5 * kblock;   // k_step, k_upd, k_fwd, k_pub, k_adj
             } else {
                 for (int i = 0; i < kblock; ++i) launch_iter(h, w, a, s);
                 PDST_CUDA(cudaGetLastError());
-                rs.launches += 4 * kblock;
+                rs.launches += 5 * kblock;   // k_step, k_upd, k_fwd, k_pub, k_adj
             }
         }
         k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out, accumulate ? 1 : 0);
