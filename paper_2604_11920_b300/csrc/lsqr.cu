@@ -1107,6 +1107,15 @@ __global__ void __launch_bounds__(LT) k_upd(int32_t n, const ST *__restrict__ vb
     }
 }
 
+// The damping sweep's shared scalars after a deferred k_upd_sweep: beta_{i+2},
+// which the forward left aside, moves in (one thread, after the join).
+__global__ void k_pub_base(LsqrScalars *base) {
+    if (threadIdx.x == 0 && base->step_pending) {
+        base->beta = base->beta_next;
+        base->step_pending = 0;
+    }
+}
+
 // Publication of the step that k_step and a deferred k_upd left in the copy
 // (one block, once both branches of the iteration have joined: the forward
 // wrote beta_{i+2} beside them).
@@ -1119,12 +1128,14 @@ __global__ void __launch_bounds__(LT) k_pub(LsqrScalars *sc, const LsqrScalars *
 // damping value l's coefficients (from k_step_sweep's copy when a step is
 // pending; the slice's last block publishes it); ||w_l||^2 to its recurrence.
 // Every block then arrives on counters[L]; the last one moves beta_next into
-// the shared scalars (all blocks have read step_pending by then).
+// the shared scalars (all blocks have read step_pending by then) -- unless
+// defer = 1 (the update running beside the forward, which still writes
+// beta_next): then k_pub_base does that after the join.
 template <class ST>
 __global__ void __launch_bounds__(LT) k_upd_sweep(int32_t n, const ST *__restrict__ vbar, double *X,
                                                   double *W, double *partial, LsqrScalars *base,
                                                   LsqrScalars *ls, LsqrScalars *stage, int L,
-                                                  unsigned *counters) {
+                                                  unsigned *counters, int defer = 0) {
     const int l = blockIdx.y;
     const bool pub = base->step_pending != 0;
     LsqrScalars *sc = ls + l;
@@ -1164,7 +1175,7 @@ __global__ void __launch_bounds__(LT) k_upd_sweep(int32_t n, const ST *__restric
         const unsigned t = atomicAdd(counters + L, 1u);
         if (t == gridDim.x * gridDim.y - 1) {
             counters[L] = 0u;
-            if (pub) {
+            if (pub && !defer) {
                 base->beta = base->beta_next;
                 base->step_pending = 0;
             }
@@ -1983,20 +1994,23 @@ static pdst_status sweep_run(pdst_handle *h, LsqrWork *w, int dtype, const doubl
         PDST_CUDA(cudaStreamSynchronize(s));
         const LsqrScalars &c = *w->h_scal;
         if (c.done || c.istop || c.err || c.itn >= c.itmax) break;
-        // the order of Solver::launch_iter, with the sweep's step and update
+        // the order of Solver::launch_iter, with the sweep's steps and updates
+        // beside the forward (the per-value scalars, x and w are theirs alone)
         for (int i = 0; i < kblock; ++i) {
             cudaEventRecord(w->ev_fork, s);
             cudaStreamWaitEvent(w->side, w->ev_fork, 0);
             k_step_sweep<<<1, LT, 0, w->side>>>(a.sc, a.lam_sc, stage, L);
+            k_upd_sweep<ST><<<gu, LT, 0, w->side>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(),
+                                                    a.sc, a.lam_sc, stage, L,
+                                                    w->sw_cnt.as<unsigned>(), 1);
             cudaEventRecord(w->ev_join, w->side);
             fwd_kernel<VT, ST, FMT>(h->nz)<<<w->grid_rows, LT, 0, s>>>(a);
             cudaStreamWaitEvent(s, w->ev_join, 0);
-            k_upd_sweep<ST><<<gu, LT, 0, s>>>(h->n, a.vbar, X, W, w->sw_part.as<double>(), a.sc,
-                                              a.lam_sc, stage, L, w->sw_cnt.as<unsigned>());
+            k_pub_base<<<1, 32, 0, s>>>(a.sc);
             adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
         }
         PDST_CUDA(cudaGetLastError());
-        launches += 4 * kblock;
+        launches += 5 * kblock;
     }
     for (int l = 0; l < L; ++l)
         k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, X + (int64_t)l * n, nullptr, m_out[l], 0);
