@@ -643,7 +643,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
 // every cell's sums go to its slots, so the result does not depend on which
 // warp took which item.  The per-warp partial slots stay zero.
 template <class VT, class ST>
-__global__ void __launch_bounds__(BT) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+__global__ void __launch_bounds__(BT, 4) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int init, double *partial,
                                              unsigned *next_item) {
     __shared__ int last_flag[WPB];
