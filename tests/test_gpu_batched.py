@@ -241,3 +241,27 @@ def test_scaled_batched_converges_faster_to_the_same_minimiser(nzc):
     with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
         fresh = pdst.build_G_problem(b[0][0], dtypes=("f32",), formats=("blocked",))
         pdst.lsqr_batched([fresh], [ds[0]], [1.0], [lams[0]], 10, 1e-6, dtype="f32", precond=1)
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_scaled_batched_generic_paths_fixed_k_match_oracle(batch, k):
+    """The scaled form on the generic paths (row stride 4 or 16 with nz = 8, 4
+    and 3: the any-nz forward and adjoint), against the oracle's scaled LSQR."""
+    b, hs = batch
+    Ds = []
+    for (p, G, D, lams), h in zip(b, hs):
+        GT = oracle.transpose(G)
+        Dc = 1.0 / np.sqrt(oracle.aug_colnorm2(GT, p.nx, p.ny, p.nz, p.w, p.lam))
+        h.set_col_scaling(to_dev(Dc))
+        Ds.append((GT, Dc))
+    ds = [to_dev(D) for _, _, D, _ in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, _, _, _ in b],
+                                       [l for _, _, _, l in b], k, 0.0, dtype="f64",
+                                       tile_rows=4, precond=1)
+    for (p, G, D, lams), (GT, Dc), mo, inf in zip(b, Ds, outs, infos):
+        got = mo.cpu().numpy()
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k, D=Dc, lam_rows=lams[j])
+            assert inf[j]["iters"] == k
+            assert rel(got[:, j], Dc * ref.x) < 1e-10, (p.nz, j, k)
