@@ -11,6 +11,8 @@ the paper's definitions:
 * ``laplacian``     3-D 7-point graph Laplacian
 * ``lsqr``          Paige & Saunders (1982) LSQR with damping / column scaling
 * ``aug_colnorm2``  squared column norms of [G; w L; lam I]
+* ``blockprec``     per-cell depth blocks of [G; w L; lam I]^T [G; w L; lam I]
+                    and the inverse Cholesky factors that precondition LSQR
 
 Parity status: every function here is pinned by tests/test_oracle_*.py
 (closed forms, dense Householder QR, SciPy's LSQR, exact recovery, LSQR
@@ -70,7 +72,7 @@ def _load():
         lib.oracle_aug_colnorm2.restype = None
         lib.oracle_apply_A.argtypes = [ctypes.c_int64, ctypes.c_int32, _i64, _i32, _d,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                       _d, ctypes.c_double, _d, _d]
+                                       _d, ctypes.c_double, _d, _d, _d]
         lib.oracle_apply_A.restype = None
         lib.oracle_apply_At.argtypes = lib.oracle_apply_A.argtypes
         lib.oracle_apply_At.restype = None
@@ -78,7 +80,7 @@ def _load():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     _d, ctypes.c_double, ctypes.c_double, _d, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _d, _d,
-                                    ctypes.c_int, _d, _d, _d, ctypes.c_int, _d, _d, _i32]
+                                    ctypes.c_int, _d, _d, _d, ctypes.c_int, _d, _d, _i32, _d]
         lib.oracle_lsqr.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -193,26 +195,40 @@ def aug_colnorm2(GT: CSR, nx: int, ny: int, nz: int, w: float, lam: float) -> np
     return out
 
 
-def apply_A(G: CSR, grid, w: float, v: np.ndarray, D=None, lam_rows: float = 0.0):
+def _blocks(P, n: int, nz: int):
+    if P is None:
+        return None
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.shape == (n // nz, nz, nz), "P: one nz x nz block per horizontal cell"
+    return P
+
+
+def apply_A(G: CSR, grid, w: float, v: np.ndarray, D=None, lam_rows: float = 0.0, P=None):
+    """y = A v with A = [G; w L], [G D; w L D; lam D] or [G P; w L P; lam P]."""
     nx, ny, nz = grid
     n = G.n_cols
+    assert D is None or P is None
     M = G.n_rows + n + (n if lam_rows > 0 else 0)
     y = np.zeros(M, dtype=np.float64)
     v = np.ascontiguousarray(v, dtype=np.float64)
     D = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    P = _blocks(P, n, nz)
     _load().oracle_apply_A(G.n_rows, n, _p(G.ptr, _i64), _p(G.idx, _i32), _p(G.val, _d),
-                           nx, ny, nz, w, _p(D, _d), lam_rows, _p(v, _d), _p(y, _d))
+                           nx, ny, nz, w, _p(D, _d), lam_rows, _p(v, _d), _p(y, _d), _p(P, _d))
     return y
 
 
-def apply_At(GT: CSR, grid, w: float, u: np.ndarray, D=None, lam_rows: float = 0.0):
+def apply_At(GT: CSR, grid, w: float, u: np.ndarray, D=None, lam_rows: float = 0.0, P=None):
+    """z = A^T u for the operators of apply_A."""
     nx, ny, nz = grid
     n = GT.n_rows
+    assert D is None or P is None
     z = np.zeros(n, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     D = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    P = _blocks(P, n, nz)
     _load().oracle_apply_At(GT.n_cols, n, _p(GT.ptr, _i64), _p(GT.idx, _i32), _p(GT.val, _d),
-                            nx, ny, nz, w, _p(D, _d), lam_rows, _p(u, _d), _p(z, _d))
+                            nx, ny, nz, w, _p(D, _d), lam_rows, _p(u, _d), _p(z, _d), _p(P, _d))
     return z
 
 
@@ -237,8 +253,10 @@ class LSQRResult:
 def lsqr(G: CSR, GT: CSR, grid, w: float, damp: float, b: np.ndarray,
          atol: float = 1e-8, btol: float = 1e-8, conlim: float = 1e8, itmax: int = 300,
          D: Optional[np.ndarray] = None, lam_rows: float = 0.0, record: int = 0,
-         history: bool = False, checkpoints=None) -> LSQRResult:
-    """LSQR on [G; w L] (or [G D; w L D; lam_rows D] when D is given).
+         history: bool = False, checkpoints=None, P: Optional[np.ndarray] = None) -> LSQRResult:
+    """LSQR on [G; w L] (or [G D; w L D; lam_rows D] when D is given, or
+    [G P; w L P; lam_rows P] with P the per-cell depth blocks, (nx*ny, nz, nz));
+    x is the solution in the scaled variables (the model is D x or P x).
 
     checkpoints: tolerances t; for each, the iterate and iteration at which a
     solve with atol = btol = t stops on S1 or S2 (the same run serves all)."""
@@ -248,6 +266,8 @@ def lsqr(G: CSR, GT: CSR, grid, w: float, damp: float, b: np.ndarray,
     b = np.ascontiguousarray(b, dtype=np.float64)
     assert b.shape[0] == m
     D = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
+    assert D is None or P is None
+    P = _blocks(P, n, nz)
     M = m + n + (n if lam_rows > 0 else 0)
     x = np.zeros(n, dtype=np.float64)
     est = np.zeros(8, dtype=np.float64)
@@ -263,7 +283,7 @@ def lsqr(G: CSR, GT: CSR, grid, w: float, damp: float, b: np.ndarray,
                          nx, ny, nz, w, _p(D, _d), lam_rows, damp, _p(b, _d),
                          atol, btol, conlim, itmax, _p(x, _d), _p(est, _d),
                          record, _p(U, _d), _p(V, _d), _p(rh, _d),
-                         nck, _p(ck, _d), _p(ck_x, _d), _p(ck_itn, _i32))
+                         nck, _p(ck, _d), _p(ck_x, _d), _p(ck_itn, _i32), _p(P, _d))
     if rc != 0:
         raise MemoryError("oracle_lsqr")
     itn = int(est[0])

@@ -23,7 +23,9 @@
  *          min ||G m - d||^2 + w^2 ||L m||^2 + damp^2 ||m||^2,
  *      with the operator A = [G; w L] and the damping handled by LSQR's own
  *      damped recurrence, or, with a right diagonal scaling m = D y, on
- *      A_D = [G D; w L D; lam D] with no recurrence damping.
+ *      A_D = [G D; w L D; lam D] with no recurrence damping, or, with a
+ *      right block-diagonal matrix P (one nz x nz block per horizontal
+ *      cell), on A_P = [G P; w L P; lam P] in the same way.
  *
  * Compile: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (no FMA
  * contraction, so the G arithmetic rounds once per written operation).
@@ -331,20 +333,44 @@ typedef struct {
     const double *D;            /* NULL or column scaling */
     double lam_rows;            /* > 0: append lam*D rows (scaled problem) */
     double *tmp_n, *tmp_n2;     /* work vectors of length n */
+    const double *P;            /* NULL or per-cell depth blocks: (nx*ny) x nz x nz, row-major */
 } op_t;
+
+/* out_h = P_h in_h for every cell h (depth-fastest column order), or with
+ * transpose != 0 out_h = P_h^T in_h.  out and in must not overlap. */
+static void blocks_apply(const double *P, int32_t n, int nz, int transpose, const double *in,
+                         double *out)
+{
+    const int32_t H = n / nz;
+    for (int32_t h = 0; h < H; ++h) {
+        const double *Ph = P + (size_t)h * nz * nz;
+        const double *x = in + (size_t)h * nz;
+        double *y = out + (size_t)h * nz;
+        for (int i = 0; i < nz; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < nz; ++k)
+                s += (transpose ? Ph[k * nz + i] : Ph[i * nz + k]) * x[k];
+            y[i] = s;
+        }
+    }
+}
 
 static int64_t op_rows(const op_t *A)
 {
     return A->m + A->n + (A->lam_rows > 0.0 ? A->n : 0);
 }
 
-/* y = A v, A = [G; w L] (times D on the right, plus lam D rows). */
+/* y = A v, A = [G; w L] (times D or the block matrix P on the right, plus
+ * lam D or lam P rows). */
 static void op_apply(const op_t *A, const double *v, double *y)
 {
     const double *vs = v;
     if (A->D) {
         for (int32_t j = 0; j < A->n; ++j)
             A->tmp_n[j] = A->D[j] * v[j];
+        vs = A->tmp_n;
+    } else if (A->P) {
+        blocks_apply(A->P, A->n, A->nz, 0, v, A->tmp_n);
         vs = A->tmp_n;
     }
     oracle_spmv(A->m, A->rp, A->ci, A->va, vs, y);
@@ -369,6 +395,10 @@ static void op_apply_t(const op_t *A, const double *u, double *z)
     if (A->D)
         for (int32_t j = 0; j < A->n; ++j)
             z[j] *= A->D[j];
+    else if (A->P) {
+        memcpy(A->tmp_n2, z, sizeof(double) * (size_t)A->n);
+        blocks_apply(A->P, A->n, A->nz, 1, A->tmp_n2, z);
+    }
 }
 
 static double norm2(int64_t len, const double *x)
@@ -388,9 +418,9 @@ static void scale(int64_t len, double a, double *x)
 /* Public operator products (used by tests for residual checks). */
 void oracle_apply_A(int64_t m, int32_t n, const int64_t *rp, const int32_t *ci,
                     const double *va, int nx, int ny, int nz, double w, const double *D,
-                    double lam_rows, const double *v, double *y)
+                    double lam_rows, const double *v, double *y, const double *P)
 {
-    op_t A = {m, n, rp, ci, va, NULL, NULL, NULL, nx, ny, nz, w, D, lam_rows, NULL, NULL};
+    op_t A = {m, n, rp, ci, va, NULL, NULL, NULL, nx, ny, nz, w, D, lam_rows, NULL, NULL, P};
     A.tmp_n = (double *)malloc(sizeof(double) * (size_t)n);
     op_apply(&A, v, y);
     free(A.tmp_n);
@@ -398,9 +428,9 @@ void oracle_apply_A(int64_t m, int32_t n, const int64_t *rp, const int32_t *ci,
 
 void oracle_apply_At(int64_t m, int32_t n, const int64_t *cp, const int32_t *ri,
                      const double *vt, int nx, int ny, int nz, double w, const double *D,
-                     double lam_rows, const double *u, double *z)
+                     double lam_rows, const double *u, double *z, const double *P)
 {
-    op_t A = {m, n, NULL, NULL, NULL, cp, ri, vt, nx, ny, nz, w, D, lam_rows, NULL, NULL};
+    op_t A = {m, n, NULL, NULL, NULL, cp, ri, vt, nx, ny, nz, w, D, lam_rows, NULL, NULL, P};
     A.tmp_n2 = (double *)malloc(sizeof(double) * (size_t)n);
     op_apply_t(&A, u, z);
     free(A.tmp_n2);
@@ -429,9 +459,9 @@ int oracle_lsqr(int64_t m, int32_t n, const int64_t *rp, const int32_t *ci,
                 double damp, const double *b, double atol, double btol, double conlim,
                 int itmax, double *x, double *est, int rec_k, double *U, double *V,
                 double *rhist, int n_ck, const double *ck_tol, double *ck_x,
-                int32_t *ck_itn)
+                int32_t *ck_itn, const double *P)
 {
-    op_t A = {m, n, rp, ci, va, cp, ri, vt, nx, ny, nz, w, D, lam_rows, NULL, NULL};
+    op_t A = {m, n, rp, ci, va, cp, ri, vt, nx, ny, nz, w, D, lam_rows, NULL, NULL, P};
     int64_t M = op_rows(&A);
     double *u = (double *)malloc(sizeof(double) * (size_t)M);
     double *Av = (double *)malloc(sizeof(double) * (size_t)M);
