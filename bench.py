@@ -6,7 +6,9 @@ Workload (default): the 64 x 64 x 16 system (65,536 unknowns; 120 stations,
 2 % noise; w = 2, lambda = 0.05), synthetic inputs from the seeded generator.
 
 One step = one solve of the chosen form (FP32 values and vectors, FP64
-scalars, column-norm scaling computed inside the step) to within 1e-4
+scalars, the per-cell depth-block preconditioner computed inside the step:
+each cell's nz x nz block of the normal matrix, its Cholesky factor R_h and
+the solve on [G P; w L P; lambda P], P_h = R_h^-1) to within 1e-4
 relative model error of the FP64 oracle's converged solution (stored in
 tests/golden by a script that calls only the oracle): the FP32 solve to tol
 1e-6, then refinement sweeps with FP32 values on the FP64 residual, their
@@ -16,7 +18,8 @@ G, replayed from CUDA graphs.  The G assembly is timed separately.
 
 Reported beside the headline: the plain FP64 GPU LSQR (FP64 values and
 vectors, element CSR/CSC, no scaling) at the same target and its own
-per-kernel roofline; the learned scaling at the same target; both forms at
+per-kernel roofline; column-norm and learned diagonal scalings and the FP64
+form with depth blocks at the same target; both forms at
 tol 1e-6 (one solve); LSMR; the damping sweep; the batched workload; compact
 records of the paper-shaped and 100 x 100 x 20 systems; the per-kernel
 roofline of the chosen form from CUDA events; the end-to-end time through
@@ -46,7 +49,8 @@ sys.path.insert(0, ROOT)
 METRIC = "LSQR time-to-tol (s) & SpMV/SpMV^T HBM GB/s vs plain FP64 GPU LSQR, 1xB300"
 
 FORMS = {
-    # name: (dtype, format, precond); precond 1 = column-norm, 2 = learned scaling
+    # name: (dtype, format, scaling); scaling 1 = column-norm, 2 = learned (both
+    # right-diagonal: the library's precond 1), 3 = per-cell depth blocks (precond 2)
     "f64-element": ("f64", "element", 0),
     "f64-blocked": ("f64", "blocked", 0),
     "df64-blocked": ("df64", "blocked", 0),
@@ -55,12 +59,16 @@ FORMS = {
     "f32-blocked-colnorm": ("f32", "blocked", 1),
     "bf16-blocked-colnorm": ("bf16", "blocked", 1),
     "f32-blocked-learned": ("f32", "blocked", 2),
+    "f32-blocked-block": ("f32", "blocked", 3),
+    "f64-blocked-block": ("f64", "blocked", 3),
 }
+LIB_PRECOND = {0: 0, 1: 1, 2: 1, 3: 2}   # scaling code of FORMS -> pdst_lsqr_opts.precond
 PLAIN = "f64-element"
 MODEL_PATH = os.path.join(ROOT, "paper_2604_11920_b300", "precond_mlp.json")
-# the chosen form: FP32 values with FP64 scalars and column-norm scaling (the
-# learned scaling is measured beside it on the same target)
-DEFAULT_FORM = "f32-blocked-colnorm"
+# the chosen form: FP32 values with FP64 scalars and the per-cell depth-block
+# preconditioner (column-norm and learned diagonal scalings are measured beside
+# it on the same target)
+DEFAULT_FORM = "f32-blocked-block"
 ACC_TARGET = 1e-4                     # relative model error vs the FP64 reference
 TOL_LADDER = (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10)
 REFINE_DTYPE = "f32"                  # refinement sweeps of the reduced-precision forms
@@ -201,9 +209,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------- roofline
 
-def algorithmic_bytes(h, p, dtype, fmt, scaled):
+def algorithmic_bytes(h, p, dtype, fmt, scaled, blocks=False):
     """Bytes each kernel must move once per launch: matrix arrays read once,
-    vectors read/written once, gathered vectors counted once (L2-resident)."""
+    vectors read/written once, gathered vectors counted once (L2-resident);
+    with depth blocks the adjoint also reads every cell's nz x nz block once."""
     vb, xb = VALUE_BYTES[dtype], VEC_BYTES[dtype]
     m, n, nnz, nz = h.m, h.n, h.nnz, p.nz
     U, H = nnz // nz, p.nx * p.ny
@@ -216,6 +225,8 @@ def algorithmic_bytes(h, p, dtype, fmt, scaled):
         adj_idx = 4 * U + 8 * (H + 1) + 4 * H
     fwd = vb * nnz + fwd_idx + 2 * xb * M + xb * n
     adj = vb * nnz + adj_idx + xb * M + 2 * xb * n + (xb * n + 8 * n if scaled else 0)
+    if blocks:
+        adj += xb * H * nz * nz - 8 * n   # the blocks replace the diagonal scaling vector
     upd = xb * n + 8 * n * 3
     return {"fwd": fwd, "adj": adj, "upd": upd}
 
@@ -255,9 +266,11 @@ def run_ncu_case(args):
     dtype, fmt, precond = FORMS[args.form]
     h = pdst.build_G_problem(p, dtypes=(dtype,), formats=(fmt,))
     d = torch.from_numpy(p.noise).cuda()
-    if precond:   # learned and column-norm scaling run the same kernels
+    if precond == 3:
+        h.set_block_precond(None, p.w, p.lam)
+    elif precond:   # learned and column-norm scaling run the same kernels
         h.set_col_scaling(None, p.w, p.lam)
-    r = h.lsqr(d, p.w, p.lam, 3, 0.0, dtype=dtype, fmt=fmt, precond=1 if precond else 0,
+    r = h.lsqr(d, p.w, p.lam, 3, 0.0, dtype=dtype, fmt=fmt, precond=LIB_PRECOND[precond],
                use_graph=False)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.form, "iters": r.info["iters"], "nnz": h.nnz}))
@@ -304,6 +317,8 @@ class System:
     def set_scaling(self, pc):
         if pc == 1:
             self.h.set_col_scaling_power(self.p.w, self.p.lam, 1.0)
+        elif pc == 3:
+            self.h.set_block_precond(None, self.p.w, self.p.lam)
         elif pc == 2:
             from paper_2604_11920_b300.train_precond import learned_scaling
             learned_scaling(self.h, self.p, self.params)   # features + MLP, inside the step
@@ -314,7 +329,7 @@ class System:
         self.set_scaling(pc)
         return self.h.lsqr(self.d, self.p.w, self.p.lam, itmax or self.p.itmax,
                            self.p.tol if tol is None else tol, dtype=dt, fmt=fm,
-                           precond=1 if pc else 0, **kw)
+                           precond=LIB_PRECOND[pc], **kw)
 
     def acc_kw(self, form, t):
         """Solve arguments of the accuracy-matched form at ladder rung t: the
@@ -373,7 +388,7 @@ def kernel_roofline(S, form, peak, iters=64, mode=2):
     pi = max(prof.info["profiled_iters"], 1)
     kms = {"fwd": prof.info["fwd_ms"] / pi, "adj": prof.info["adj_ms"] / pi,
            "upd": prof.info["upd_ms"] / pi}
-    ab = algorithmic_bytes(S.h, S.p, dt, fm, pc > 0)
+    ab = algorithmic_bytes(S.h, S.p, dt, fm, pc > 0, blocks=pc == 3)
     gbs = {k: ab[k] / (kms[k] * 1e-3) / 1e9 for k in ("fwd", "adj")}
     return {"kernel_ms_per_iter": {k: round(v, 5) for k, v in kms.items()},
             "gbs": {k: round(v, 1) for k, v in gbs.items()},
@@ -490,9 +505,11 @@ def run_pdst(args, rank, world):
         else:
             accuracy["plain_fp64"] = {"form": PLAIN, "tol": None, "calibration": pcal,
                                       "kernels": plain_roof}
-        # the other forms at the same target, for comparison: learned scaling,
-        # and BF16 values for the first solve (the refinement sweeps stay FP32)
-        for other in ("f32-blocked-colnorm", "f32-blocked-learned", "bf16-blocked-colnorm"):
+        # the other forms at the same target, for comparison: the diagonal
+        # scalings (column norms, learned), BF16 values for the first solve (the
+        # refinement sweeps stay FP32) and the depth blocks in FP64 (one solve)
+        for other in ("f32-blocked-block", "f64-blocked-block", "f32-blocked-colnorm",
+                      "f32-blocked-learned", "bf16-blocked-colnorm"):
             if other == args.form or (other.endswith("learned") and params is None):
                 continue
             oc = calibrate(S, other, relerr, stream)
@@ -570,7 +587,7 @@ def run_pdst(args, rank, world):
         def host_step():
             S.set_scaling(pc_)
             h.lsqr_host(dn, p.w, p.lam, itmax_h, tol_h, m_out=mn, dtype=dt_, fmt=fm_,
-                        precond=min(pc_, 1), **hkw)
+                        precond=LIB_PRECOND[pc_], **hkw)
         host_step()
         barrier()
         torch.cuda.synchronize()

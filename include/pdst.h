@@ -155,7 +155,10 @@ typedef struct {
     double atol;       /* < 0: use tol */
     double btol;       /* < 0: use tol */
     double conlim;     /* <= 0: 1e8 */
-    int32_t precond;   /* 0 none; 1 right diagonal scaling set by pdst_set_col_scaling */
+    int32_t precond;   /* 0 none; 1 right diagonal scaling set by pdst_set_col_scaling;
+                          2 right block-diagonal preconditioner (one nz x nz block per
+                          horizontal cell) set by pdst_set_block_precond: blocked format,
+                          nz <= 32, dtype F64, F32 or BF16 (refine_dtype likewise) */
     int32_t kblock;    /* iterations per graph launch (<= 0: 16) */
     int32_t use_graph; /* 1 (default): CUDA graph replay; 0: plain launches */
     int32_t profile;   /* per-kernel device time in pdst_lsqr_info: 1, one iteration per
@@ -218,8 +221,10 @@ typedef struct {
  * A = [G; w L] with damping lambda in the recurrence, or, with
  * opts->precond = 1 and a scaling D set by pdst_set_col_scaling, on
  * A_D = [G D; w L D; lambda D] with no recurrence damping and m = D y (the
- * same minimiser).  d_dev: m_rows FP64 (device, caller-owned).  m_out_dev: n
- * FP64 (device, caller-owned).  tol sets atol = btol unless opts overrides;
+ * same minimiser), or, with opts->precond = 2 and the blocks P set by
+ * pdst_set_block_precond, on A_P = [G P; w L P; lambda P] and m = P y.
+ * d_dev: m_rows FP64 (device, caller-owned).  m_out_dev: n FP64 (device,
+ * caller-owned).  tol sets atol = btol unless opts overrides;
  * conlim defaults to 1e8.  The Golub-Kahan scalars, the rotations, the norm
  * estimates and the x/w update are FP64 in every dtype.  info (host) may be
  * NULL.  The call is synchronous on `stream`.
@@ -245,8 +250,8 @@ pdst_status pdst_lsqr(pdst_handle_t h, const double *d_dev, double w, double lam
  *
  * Arguments and results are those of pdst_lsqr (same kernels in the same
  * order, same answer bit for bit); the iterations are plain kernel launches
- * (opts->use_graph is ignored), opts->profile and opts->refine must be 0 and
- * opts->method PDST_LSQR (PDST_ERR_ARG otherwise).  The handle's device must
+ * (opts->use_graph is ignored), opts->profile and opts->refine must be 0,
+ * opts->precond 0 or 1 and opts->method PDST_LSQR (PDST_ERR_ARG otherwise).  The handle's device must
  * be the current device.  The first call on a device looks up the array's
  * device address there (cudaGetSymbolAddress) and keeps it for later calls;
  * make that first call before any stream capture, and do not call this
@@ -300,6 +305,40 @@ pdst_status pdst_lsqr_host(pdst_handle_t h, const double *d_host, double w, doub
  */
 pdst_status pdst_set_col_scaling(pdst_handle_t h, const double *D_dev, double w, double lambda,
                                  void *stream);
+
+/*
+ * Per-cell depth-block right preconditioner (precond = 2).  The nz columns of
+ * one horizontal cell h (Eq. 7's depth-fastest order: j = h*nz + k) are
+ * strongly coupled: each row of G (Eq. 5) touches all of them through one
+ * depth kernel, and L couples neighbouring depths.  Let A = [G; w L; lambda I]
+ * and A_h its nz columns of cell h; the preconditioner factors the diagonal
+ * block B_h = A_h^T A_h of the normal matrix as B_h = R_h^T R_h (Cholesky,
+ * R_h upper triangular with a positive diagonal) and runs LSQR on A P with
+ * P = blockdiag(P_h), P_h = R_h^{-1}, so that every cell's column group of
+ * A P is orthonormal (the block form of column-norm scaling).  m = P y.
+ *
+ * pdst_depth_blocks: B_h for every cell into B_dev, (nx*ny) x nz x nz FP64,
+ *   row-major per cell (entry (h, i, k) at (h*nz + i)*nz + k), from the FP64
+ *   values of G when kept, else the FP32 or BF16 ones widened; device,
+ *   caller-owned.  Asynchronous on `stream`.
+ * pdst_set_block_precond: P_dev NULL computes B_h as above and P_h = R_h^{-1}
+ *   in FP64 on the device for the given w, lambda; otherwise P_dev holds the
+ *   blocks in the same layout (device, copied; only the upper triangle is
+ *   read, the lower one is taken as zero).  The handle keeps P in FP64 and an
+ *   FP32 copy (used by the F32 and BF16 forms).  Needs nz <= 32.
+ *   Synchronous.  PDST_ERR_BREAKDOWN when a block is not positive definite
+ *   (a cell no ray crosses with w = lambda = 0); the handle then keeps no
+ *   preconditioner.
+ * pdst_get_block_precond: copies the FP64 blocks P into P_dev_out (same
+ *   layout).  PDST_ERR_STATE if none is set.  Synchronous.
+ * Errors: PDST_ERR_ARG (NULL handle or output, non-finite or negative w or
+ * lambda), PDST_ERR_LIMIT (nz > 32), PDST_ERR_OOM, PDST_ERR_CUDA.
+ */
+pdst_status pdst_depth_blocks(pdst_handle_t h, double w, double lambda, double *B_dev,
+                              void *stream);
+pdst_status pdst_set_block_precond(pdst_handle_t h, const double *P_dev, double w, double lambda,
+                                   void *stream);
+pdst_status pdst_get_block_precond(pdst_handle_t h, double *P_dev_out, void *stream);
 
 typedef struct {
     int32_t tile_rows;        /* G rows per forward work item; 0 = chosen by the autotuner,
@@ -445,8 +484,8 @@ typedef struct {
     double z0_factor;      /* kernel depth per period (default 1.2 km/s) */
     double kernel_power;   /* a above (default 1; 0: the kernels do not follow the model) */
     pdst_lsqr_opts inner;  /* options of each update's solve (pdst_lsqr); with precond = 1
-                              the column-norm scaling of the current G is set before each
-                              solve */
+                              the column-norm scaling of the current G, with precond = 2 its
+                              depth-block preconditioner, is set before each solve */
 } pdst_outer_opts;
 
 /* Fill *o with the defaults listed above (inner: pdst_lsqr_opts_default). */

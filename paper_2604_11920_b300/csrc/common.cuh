@@ -196,6 +196,11 @@ struct pdst_handle {
 
     pdst::DevBuf colscale;     // double [n] right diagonal scaling D
     bool has_colscale = false;
+    pdst::DevBuf blkP64;       // double [H*nz*nz] per-cell depth blocks P_h (upper triangular)
+    pdst::DevBuf blkP32;       // float  [H*nz*nz] the same, rounded (F32 and BF16 forms)
+    pdst::DevBuf blkP64T;      // double [H*nz*nz] P_h^T per cell (row-major), for coalesced
+    pdst::DevBuf blkP32T;      // float  [H*nz*nz]   reads of the rows of P_h
+    bool has_blkprec = false;
 
     pdst::LsqrWork *work = nullptr;
     ~pdst_handle() { pdst::destroy_work(work); }

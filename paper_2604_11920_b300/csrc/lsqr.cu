@@ -68,7 +68,9 @@ template <class VT, class ST> struct OpArgs {
     ST *chunk_part;           // n_adj x nz partial column sums (multi-chunk cells)
     unsigned *cell_done;      // H finished-chunk counters
     const double *D;          // right diagonal scaling or nullptr
-    int lam_rows_on;          // append lambda*D rows
+    const void *Pb;           // per-cell depth blocks P_h (ST-typed, H x nz x nz) or nullptr
+    const void *PbT;          // the blocks transposed (P_h^T, row-major)
+    int lam_rows_on;          // append lambda*D (or lambda*P) rows
     ST *ubar;                 // M = m + n (+ n)
     ST *vbar;                 // n
     ST *vsc;                  // n: D o v-bar (== vbar when no scaling)
@@ -487,6 +489,71 @@ __device__ __forceinline__ double adj_finish(const OpArgs<VT, ST> &a, int64_t j,
     return (double)v * (double)v;
 }
 
+// The per-cell finish with the depth-block preconditioner P = blockdiag(P_h)
+// (P_h upper triangular, nz <= 32): lane k < nz holds the cell's G^T u sum of
+// depth k.  s = (A^T u)_h (stencil and lambda terms added per lane),
+// t = P_h^T s, v-bar_h <- t / beta - (beta/alpha) v-bar_h, and the forward's
+// input P_h v-bar_h; both products by shuffles over the cell's lanes, their
+// block entries read row by row (P_h for t, P_h^T for P_h v: each read of a
+// row is one contiguous segment across the lanes), eight at a time.  With
+// nz <= 16 the two half-warps each take half of every sum's terms and add
+// the halves with one shuffle.  Returns this lane's v-bar^2.
+template <class VT, class ST>
+__device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_t h, ST dot,
+                                                 ST ib, ST cv, ST wsm, ST lamr, int init,
+                                                 int lane) {
+    using AT = ST;
+    constexpr int CH = 8;
+    const int nz = a.nz;
+    const bool split = nz <= 16;
+    const int k = split ? (lane & 15) : lane;     // the output depth this lane sums for
+    const bool on = k < nz;
+    const bool own = lane < nz;                   // the lane that holds depth k's values
+    const int ih = split ? (nz + 1) >> 1 : nz;    // terms per half
+    const int i0 = (split && lane >= 16) ? ih : 0;
+    const int64_t j = h * nz + lane;
+    AT sj = 0;
+    if (own) {
+        sj = dot + wsm * laplace<AT, ST>(a.ubar + a.m, j, a.nx, a.ny, a.nz);
+        if (a.lam_rows_on) sj += lamr * (AT)a.ubar[a.m + a.n + j];
+    }
+    const ST *P = static_cast<const ST *>(a.Pb) + h * nz * nz;
+    const ST *PT = static_cast<const ST *>(a.PbT) + h * nz * nz;
+    // t_k = sum_{i <= k} P[i][k] s_i over this half's terms i0 .. i0 + ih - 1
+    AT t = 0;
+    for (int u0 = 0; u0 < ih; u0 += CH) {
+        AT pv[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int i = i0 + u0 + u;
+            pv[u] = (on && u0 + u < ih && i < nz && i <= k) ? (AT)P[i * nz + k] : (AT)0;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) t += pv[u] * __shfl_sync(FULL, sj, (i0 + u0 + u) & 31);
+    }
+    if (split) t += __shfl_xor_sync(FULL, t, 16);
+    AT v = 0;
+    if (own) {
+        v = init ? t * ib : t * ib - cv * a.vbar[j];
+        a.vbar[j] = v;
+    }
+    // q_k = sum_{i >= k} P[k][i] v_i = sum_{i >= k} P^T[i][k] v_i
+    AT q = 0;
+    for (int u0 = 0; u0 < ih; u0 += CH) {
+        AT pv[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int i = i0 + u0 + u;
+            pv[u] = (on && u0 + u < ih && i < nz && i >= k) ? (AT)PT[i * nz + k] : (AT)0;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) q += pv[u] * __shfl_sync(FULL, v, (i0 + u0 + u) & 31);
+    }
+    if (split) q += __shfl_xor_sync(FULL, q, 16);
+    if (own) a.vsc[j] = q;
+    return (double)v * (double)v;
+}
+
 // G^T rows of the adjoint sweep in the blocked CSC layout.  Work item = a
 // chunk of up to adj_chunk rows of one cell (cells longest first).  A row's
 // nz values are contiguous, so L = nz / G lanes share a row, each reading G
@@ -639,11 +706,16 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
         }
         if (finish) {
             double css = 0.0;
+            if (a.Pb) {
+                css = adj_finish_blk(a, (int64_t)h, dot[0], ib, cv, wsm, lamr, init, lane);
+            } else {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int k = lane + 32 * half;
-                if (k < nz)
-                    css += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr, init);
+                for (int half = 0; half < 2; ++half) {
+                    const int k = lane + 32 * half;
+                    if (k < nz)
+                        css += adj_finish(a, (int64_t)h * nz + k, dot[half], ib, cv, wsm, lamr,
+                                          init);
+                }
             }
             // the cell's sum goes to its slot (which warp, and which of a
             // split cell's items, finishes it depends on arrival order); the
@@ -1192,6 +1264,31 @@ __global__ void k_finalize(int32_t n, const double *__restrict__ x, const double
     }
 }
 
+// (P y)_j = sum_{i >= k} P_h[k][i] y_{h nz + i}  (j = h nz + k; P_h upper
+// triangular, in the precision the solve used, widened to FP64).
+template <class ST>
+__device__ __forceinline__ double blk_apply_row(const ST *__restrict__ P,
+                                                const double *__restrict__ y, int64_t j, int nz) {
+    const int64_t h = j / nz;
+    const int k = (int)(j - h * nz);
+    const ST *Pr = P + (h * nz + k) * nz;
+    const double *yh = y + h * nz;
+    double s = 0.0;
+    for (int i = k; i < nz; ++i) s += (double)Pr[i] * yh[i];
+    return s;
+}
+
+// m = P x (or m += P x) with the depth-block preconditioner.
+template <class ST>
+__global__ void k_finalize_blk(int32_t n, int nz, const double *__restrict__ x,
+                               const ST *__restrict__ P, double *m_out, int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = blk_apply_row(P, x, j, nz);
+        m_out[j] = accumulate ? m_out[j] + v : v;
+    }
+}
+
 // y = G x or G^T x with FP64 vectors (pdst_apply_G).
 template <class VT, int FMT>
 __global__ void __launch_bounds__(LT) k_spmv(OpArgs<VT, double> a, int trans,
@@ -1251,6 +1348,7 @@ __global__ void __launch_bounds__(LT) k_colnorm_scale(OpArgs<VT, double> a, doub
 
 struct LsqrWork {
     int dtype = -1, format = -1, lamrows = -1;
+    int blk = 0;                     // the solve runs with the depth-block preconditioner
     const void *graph_D = nullptr;
     int64_t M = 0;
     DevBuf ubar, vbar, vsc, x, wv, hbar, partial, scal, sync, chunk_part, cell_done, cell_ss;
@@ -1302,6 +1400,12 @@ static OpArgs<VT, ST> make_args(pdst_handle *h, int dtype, LsqrWork *w, bool sca
     a.n_cells = h->H;
     a.n_adj = h->n_adj;
     a.D = scaled ? h->colscale.as<double>() : nullptr;
+    a.Pb = a.PbT = nullptr;
+    if (w && w->blk) {
+        a.D = nullptr;
+        a.Pb = sizeof(ST) == sizeof(double) ? h->blkP64.p : h->blkP32.p;
+        a.PbT = sizeof(ST) == sizeof(double) ? h->blkP64T.p : h->blkP32T.p;
+    }
     a.lam_rows_on = lamrows ? 1 : 0;
     if (w) {
         a.ubar = w->ubar.as<ST>();
@@ -1581,7 +1685,12 @@ template <class VT, class ST, int FMT> struct Solver {
                 rs.launches += 5 * kblock;   // k_step, k_upd, k_fwd, k_pub, k_adj
             }
         }
-        k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out, accumulate ? 1 : 0);
+        if (a.Pb)
+            k_finalize_blk<ST><<<w->grid_vec, LT, 0, s>>>(h->n, h->nz, a.x,
+                                                          static_cast<const ST *>(a.Pb), m_out,
+                                                          accumulate ? 1 : 0);
+        else
+            k_finalize<<<w->grid_vec, LT, 0, s>>>(h->n, a.x, a.D, m_out, accumulate ? 1 : 0);
         PDST_CUDA(cudaGetLastError());
         rs.launches += 1;
         PDST_CUDA(cudaMemcpyAsync(w->h_scal, w->scal.p, sizeof(LsqrScalars),
@@ -1628,13 +1737,16 @@ __global__ void __launch_bounds__(LT) k_resid(OpArgs<double, double> a, const do
     }
 }
 
-// out[0] = ||D x||^2, out[1] = ||m||^2 (one block, fixed order).
+// out[0] = ||D x||^2 (or ||P x||^2 with depth blocks P), out[1] = ||m||^2
+// (one block, fixed order).
+template <class ST>
 __global__ void k_corr_norms(int32_t n, const double *__restrict__ x, const double *__restrict__ D,
-                             const double *__restrict__ mv, double *out) {
+                             const double *__restrict__ mv, double *out,
+                             const ST *__restrict__ P = nullptr, int nz = 1) {
     __shared__ double s0[32], s1[32];
     double a = 0.0, b = 0.0;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const double c = D ? D[j] * x[j] : x[j];
+        const double c = P ? blk_apply_row(P, x, j, nz) : (D ? D[j] * x[j] : x[j]);
         a += c * c;
         b += mv[j] * mv[j];
     }
@@ -1693,12 +1805,26 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
         return PDST_ERR_LIMIT;
     }
     const bool user_scaled = opts.precond == 1;
+    const bool user_blk = opts.precond == 2;
     if (user_scaled && !h->has_colscale) {
         set_error("pdst_lsqr: precond = 1 needs pdst_set_col_scaling first");
         return PDST_ERR_STATE;
     }
-    PDST_CHECK_ARG(opts.precond == 0 || opts.precond == 1, "pdst_lsqr: unknown precond %d",
+    PDST_CHECK_ARG(opts.precond >= 0 && opts.precond <= 2, "pdst_lsqr: unknown precond %d",
                    opts.precond);
+    if (user_blk) {
+        if (!h->has_blkprec) {
+            set_error("pdst_lsqr: precond = 2 needs pdst_set_block_precond first");
+            return PDST_ERR_STATE;
+        }
+        PDST_CHECK_ARG(fmt == PDST_FMT_BLOCKED, "pdst_lsqr: precond = 2 runs on the blocked layout");
+        PDST_CHECK_ARG(dtype != PDST_DF64 && opts.refine_dtype != PDST_DF64,
+                       "pdst_lsqr: precond = 2 is not available in the double-float form");
+        if (h->nz > 32) {
+            set_error("pdst_lsqr: precond = 2 needs nz <= 32");
+            return PDST_ERR_LIMIT;
+        }
+    }
     PDST_CHECK_ARG(opts.refine >= 0 && opts.refine <= 100, "pdst_lsqr: refine must be in 0..100");
     const bool refine = opts.refine > 0;
     PDST_CHECK_ARG(opts.refine_dtype >= -1 && opts.refine_dtype <= 3,
@@ -1722,7 +1848,7 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     // refinement sweeps solve for a correction with a full augmented right-hand
     // side, so they always use the form with explicit lambda rows (unit scaling
     // when none is set)
-    const bool scaled = user_scaled || refine;
+    const bool scaled = user_scaled || user_blk || refine;
     const bool lamrows = scaled && lam > 0.0;
     PDST_CHECK_ARG(opts.profile >= 0 && opts.profile <= 2, "pdst_lsqr: unknown profile mode %d",
                    opts.profile);
@@ -1746,14 +1872,18 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
     LsqrWork *w = h->work;
     const bool fresh = w->dtype != dtype || w->format != fmt || w->lamrows != (int)lamrows;
     const double *Dover = nullptr;
-    if (refine && !user_scaled) {
+    w->blk = user_blk ? 1 : 0;
+    if (refine && !user_scaled && !user_blk) {
         PDST_TRY(w->ones.alloc(sizeof(double) * std::max<int32_t>(h->n, 1)));
         k_fill<<<num_sms(h->device) * 4, LT, 0, s>>>(h->n, 1.0, w->ones.as<double>());
         PDST_CUDA(cudaGetLastError());
         Dover = w->ones.as<double>();
     }
     // captured graphs hold the workspace and scaling pointers: rebuild on change
-    const void *dptr = Dover ? (const void *)Dover : (user_scaled ? h->colscale.p : nullptr);
+    const void *dptr = Dover         ? (const void *)Dover
+                       : user_scaled ? h->colscale.p
+                       : user_blk    ? h->blkP64.p
+                                     : nullptr;
     if (fresh || w->graph_D != dptr) {
         for (auto &g : w->graphs)
             if (g.second) cudaGraphExecDestroy(g.second);
@@ -1850,8 +1980,17 @@ static pdst_status lsqr_impl(pdst_handle *h, const double *d_dev, double w_s, do
             ++sweeps;
             if (w->h_scal->err) break;
             const double *Dp = Dover ? Dover : h->colscale.as<double>();
-            k_corr_norms<<<1, 1024, 0, s>>>(h->n, w->x.as<double>(), Dp, m_out,
-                                            w->corr.as<double>());
+            if (user_blk && sd == PDST_F64)
+                k_corr_norms<double><<<1, 1024, 0, s>>>(h->n, w->x.as<double>(), nullptr, m_out,
+                                                        w->corr.as<double>(),
+                                                        h->blkP64.as<double>(), h->nz);
+            else if (user_blk)
+                k_corr_norms<float><<<1, 1024, 0, s>>>(h->n, w->x.as<double>(), nullptr, m_out,
+                                                       w->corr.as<double>(),
+                                                       h->blkP32.as<float>(), h->nz);
+            else
+                k_corr_norms<double><<<1, 1024, 0, s>>>(h->n, w->x.as<double>(), Dp, m_out,
+                                                        w->corr.as<double>());
             rs.launches += 1;
             double cn[2];
             PDST_CUDA(cudaMemcpyAsync(cn, w->corr.p, sizeof(cn), cudaMemcpyDeviceToHost, s));
@@ -2091,6 +2230,7 @@ static pdst_status sweep_impl(pdst_handle *h, const double *d_dev, double w_s, i
     }
     if (!h->work) h->work = new LsqrWork();
     LsqrWork *w = h->work;
+    w->blk = 0;   // the sweep runs unpreconditioned
     const bool fresh = w->dtype != dtype || w->format != fmt || w->lamrows != 0;
     if (fresh) {
         // buffers may move: the ordinary solve's captured graphs are stale

@@ -158,6 +158,8 @@ extern "C" pdst_status pdst_outer_loop(pdst_handle_t h, const double *d_obs_dev,
         // Eq. 6 for the update, on G of the current model
         if (o.inner.precond == 1)
             PDST_TRY(pdst_set_col_scaling(h, nullptr, w, lambda, stream));
+        else if (o.inner.precond == 2)
+            PDST_TRY(pdst_set_block_precond(h, nullptr, w, lambda, stream));
         pdst_lsqr_info li{};
         PDST_TRY(pdst_lsqr(h, r.as<double>(), w, lambda, itmax, tol, dm.as<double>(), &li,
                            &o.inner, stream));

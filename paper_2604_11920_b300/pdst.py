@@ -121,6 +121,9 @@ SIGNATURES = {
     "pdst_col_norms": (_i32, [_vp, _d, _d, _vp, _vp]),
     "pdst_set_col_scaling_power": (_i32, [_vp, _d, _d, _d, _vp]),
     "pdst_precond_features": (_i32, [_vp, _vp, _vp, _vp]),
+    "pdst_depth_blocks": (_i32, [_vp, _d, _d, _vp, _vp]),
+    "pdst_set_block_precond": (_i32, [_vp, _vp, _d, _d, _vp]),
+    "pdst_get_block_precond": (_i32, [_vp, _vp, _vp]),
     "pdst_mlp_forward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "pdst_mlp_grad": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "pdst_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _i64, _d, _d, _d, _d, _vp]),
@@ -380,6 +383,37 @@ class Handle:
         import torch
         p = ctypes.c_void_p(None) if D is None else _dev_ptr(D, self.n, torch.float64, "D")
         _check(load().pdst_set_col_scaling(self.ptr, p, w, lam, _stream(stream)))
+
+    def _block_count(self):
+        nz = self.grid.nz
+        return (self.n // nz) * nz * nz if nz else 0
+
+    def depth_blocks(self, w, lam, stream=None):
+        """pdst_depth_blocks: (nx*ny, nz, nz) float64 CUDA tensor of B_h."""
+        import torch
+        B = torch.empty(self._block_count(), dtype=torch.float64, device="cuda")
+        _check(load().pdst_depth_blocks(self.ptr, float(w), float(lam),
+                                        _dev_ptr(B, B.numel(), torch.float64, "B"),
+                                        _stream(stream)))
+        return B.view(-1, self.grid.nz, self.grid.nz)
+
+    def set_block_precond(self, P=None, w=0.0, lam=0.0, stream=None):
+        """pdst_set_block_precond: P (nx*ny, nz, nz) float64 CUDA tensor, or
+        None to compute P_h = R_h^{-1} from the depth blocks for w, lam."""
+        import torch
+        if P is None:
+            p = ctypes.c_void_p(None)
+        else:
+            P = P.contiguous()
+            p = _dev_ptr(P.view(-1), self._block_count(), torch.float64, "P")
+        _check(load().pdst_set_block_precond(self.ptr, p, float(w), float(lam), _stream(stream)))
+
+    def get_block_precond(self, stream=None):
+        import torch
+        P = torch.empty(self._block_count(), dtype=torch.float64, device="cuda")
+        _check(load().pdst_get_block_precond(self.ptr, _dev_ptr(P, P.numel(), torch.float64, "P"),
+                                             _stream(stream)))
+        return P.view(-1, self.grid.nz, self.grid.nz)
 
 
 def build_G(nx, ny, nz, dx_km, dz_km, ctrl, row_period, n_periods, kdz, dtypes=("f64", "f32"),
