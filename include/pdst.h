@@ -350,7 +350,10 @@ typedef struct {
     int32_t precond;          /* 0 none; 1 each system's right diagonal scaling set by
                                  pdst_set_col_scaling on its handle: pair (s, j) solves
                                  A_D = [G D; w L D; lambda_j D] with no recurrence damping and
-                                 returns m = D y (the same minimiser) */
+                                 returns m = D y (the same minimiser); 2 each system's
+                                 depth blocks P set by pdst_set_block_precond on its handle
+                                 (A_P = [G P; w L P; lambda_j P], m = P y; one kernel more
+                                 per iteration finishes each cell) */
     int32_t reserved;
 } pdst_batched_opts;
 

@@ -33,6 +33,12 @@ constexpr int RMAX = 16;     // right-hand sides per system (lanes of a half-war
 constexpr int LCOLS = 32;    // columns per stencil / update work item
 constexpr int NB = 8;        // work buffers per system: U, V, X, W, chunk sums, chunk counters,
                              // cell sums, scaled V
+//
+// With the per-cell depth-block preconditioner (precond = 2) the adjoint
+// leaves s = A^T u (stencil and lambda rows included) in Vs, and k_bblk, one
+// half-warp per cell with lane j = right-hand side j, finishes each cell:
+// t = P_h^T s, v-bar <- t / beta - (beta/alpha) v-bar, Vs <- P_h v-bar, and
+// the cell's sums of squares (one launch more per iteration).
 
 template <class VT, class ST> struct BSys {
     int64_t m;
@@ -55,8 +61,10 @@ template <class VT, class ST> struct BSys {
     double *cell_ss;           // H x RMAX: sum of v^2 of cells finished across several items
     ST *U;            // (m + n [+ n]) x RS, right-hand side fastest (padding lanes stay 0)
     ST *V;            // n x RS, right-hand side fastest (padding lanes stay 0)
-    ST *Vs;           // n x RS: D o V with a right scaling, else V itself
+    ST *Vs;           // n x RS: D o V (or P V) with a right scaling, else V itself; with depth
+                      // blocks it holds (A^T u) between the adjoint and k_bblk
     const double *D;  // right diagonal scaling D (n) or nullptr
+    const ST *P;      // per-cell depth blocks P_h (H x nz x nz, upper triangular) or nullptr
     int32_t lamr;     // 1: the lambda_j D rows are appended (scaled form)
     double *X, *W;    // n x R
     const double *d;  // m x R
@@ -514,6 +522,10 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
                 if (!upd[b]) continue;
                 AT sv = acc[a][b] + wsm * lap[b];
                 if (S.lamr) sv += lr[b] * (AT)S.U[(S.m + S.n + jc) * 16 + 4 * g + b];
+                if (S.P) {   // finished by k_bblk
+                    S.Vs[jc * 16 + 4 * g + b] = sv;
+                    continue;
+                }
                 if (S.D) sv *= dj;
                 const AT v = init ? sv * ib[b] : sv * ib[b] - cv[b] * vp[b];
                 vp[b] = v;
@@ -537,7 +549,7 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
     const double r = cpt == 0 ? q[0] : cpt == 1 ? q[1] : cpt == 2 ? q[2] : q[3];
     // the cell's sums go to its slots, added in cell order by k_bred (which
     // warp, and which item of a split cell, finishes the cell varies)
-    if (finish && lane < 16) S.cell_ss[(int64_t)h * RMAX + j] = r;
+    if (finish && lane < 16 && !S.P) S.cell_ss[(int64_t)h * RMAX + j] = r;
     return 0.0;
 }
 
@@ -623,6 +635,10 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
             AT sv = acc[k] + wsm * laplace_strided<AT, ST>(S.U + S.m * RS, jc, RS, j, S.nx,
                                                            S.ny, nz);
             if (S.lamr) sv += (AT)c.lam * (AT)S.U[(S.m + S.n + jc) * RS + j];
+            if (S.P) {   // finished by k_bblk
+                S.Vs[jc * RS + j] = sv;
+                continue;
+            }
             const AT dj = S.D ? (AT)S.D[jc] : (AT)1;
             if (S.D) sv *= dj;
             ST *vp = S.V + jc * RS + j;
@@ -632,7 +648,7 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
             ss += (double)v * (double)v;
         }
     }
-    if (finish && half == 0 && j < R) S.cell_ss[(int64_t)h * RMAX + j] = ss;
+    if (finish && half == 0 && j < R && !S.P) S.cell_ss[(int64_t)h * RMAX + j] = ss;
     return 0.0;
 }
 
@@ -718,6 +734,86 @@ __global__ void k_bfinal(int64_t n, int R, const double *__restrict__ D, const d
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x)
         m_out[i] = D ? D[i / R] * X[i] : X[i];
+}
+
+// m = P x with the depth blocks: m[(h nz + k) R + j] = sum_{i >= k} P_h[k][i] x[(h nz + i) R + j].
+template <class ST>
+__global__ void k_bfinal_blk(int64_t n, int nz, int R, const ST *__restrict__ P,
+                             const double *__restrict__ X, double *m_out) {
+    const int64_t total = n * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = e / R;
+        const int j = (int)(e - col * R);
+        const int64_t h = col / nz;
+        const int k = (int)(col - h * nz);
+        const ST *Pr = P + (h * nz + k) * nz;
+        double sum = 0.0;
+        for (int i = k; i < nz; ++i) sum += (double)Pr[i] * X[(h * nz + i) * R + j];
+        m_out[e] = sum;
+    }
+}
+
+// The depth-block finish of the adjoint (precond = 2): half-warp per cell (two
+// cells per warp item), lane j = right-hand side j.  Reads s = A^T u from Vs,
+// t = P_h^T s (in place, depths descending), v-bar = t / beta - (beta/alpha)
+// v-bar (start step: t / beta), Vs = P_h v-bar; the cell's sum of v-bar^2 per
+// right-hand side goes to its slot (added in cell order by k_bred).  The
+// blocks are read once per cell and broadcast to the lanes.
+template <class VT, class ST>
+__global__ void __launch_bounds__(BT) k_bblk(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
+                                             int64_t nitems, int init) {
+    using AT = ST;
+    const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int s = find_sys(beg, nsys, it);
+        const BSys<VT, ST> &S = sys[s];
+        const int nz = S.nz;
+        const int64_t H = S.n / nz;
+        const int64_t h = 2 * (it - beg[s]) + half;
+        if (S.active == 0 || h >= H || j >= S.R) continue;
+        const Col c = col_state(S.sc, j, S.R);
+        const bool upd = c.act && (init || c.beta > 0.0);
+        double ss = 0.0;
+        if (upd) {
+            const AT ib = c.beta > 0.0 ? (AT)(1.0 / c.beta) : (AT)0;
+            const AT cv = init ? (AT)0 : (c.alpha > 0.0 ? (AT)(c.beta / c.alpha) : (AT)0);
+            const ST *P = S.P + h * nz * nz;
+            const int64_t c0 = h * nz;
+            AT a[BNZ];
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k) a[k] = k < nz ? (AT)S.Vs[(c0 + k) * S.RS + j] : (AT)0;
+#pragma unroll
+            for (int k = BNZ - 1; k >= 0; --k) {
+                if (k >= nz) continue;
+                AT t = 0;
+#pragma unroll
+                for (int i = 0; i <= k; ++i) t += (AT)P[i * nz + k] * a[i];
+                a[k] = t;
+            }
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k) {
+                if (k >= nz) continue;
+                ST *vp = S.V + (c0 + k) * S.RS + j;
+                const AT v = init ? a[k] * ib : a[k] * ib - cv * *vp;
+                *vp = v;
+                a[k] = v;
+                ss += (double)v * (double)v;
+            }
+#pragma unroll
+            for (int k = 0; k < BNZ; ++k) {
+                if (k >= nz) continue;
+                AT q = 0;
+#pragma unroll
+                for (int i = k; i < BNZ; ++i)
+                    if (i < nz) q += (AT)P[k * nz + i] * a[i];
+                S.Vs[(c0 + k) * S.RS + j] = q;
+            }
+        }
+        S.cell_ss[h * RMAX + j] = ss;
+    }
 }
 
 // One block of 256 threads per system: thread (l, j) sums the partials of the
@@ -827,12 +923,13 @@ struct BatchWork {
     int TR = 0;
     bool tuned = false;
     std::vector<DevBuf *> bufs;
-    DevBuf desc, scal, partial, fbeg, abeg, ubeg, active, adj_ctr;
+    DevBuf desc, scal, partial, fbeg, abeg, ubeg, bbeg, active, adj_ctr;
     int *h_active = nullptr;
     LsqrScalars *h_scal = nullptr;
-    int64_t nf_items = 0, na_items = 0, nu_items = 0;
-    unsigned gi = 1, gf = 1, ga = 1, gu = 1;   // grids of init / forward / adjoint / update
-    std::vector<int64_t> hf, ha, hu;
+    int64_t nf_items = 0, na_items = 0, nu_items = 0, nb_items = 0;
+    unsigned gi = 1, gf = 1, ga = 1, gu = 1, gb = 1;   // grids of init / forward / adjoint /
+                                                       // update / depth-block finish
+    std::vector<int64_t> hf, ha, hu, hb;
     std::map<int, cudaGraphExec_t> graphs;
     std::vector<double> tune_ms;
     ~BatchWork() {
@@ -880,25 +977,30 @@ template <class VT, class ST> struct Batched {
     static pdst_status prepare(BatchWork *bw, const std::vector<pdst_handle *> &hs,
                                const int32_t *nrhs, int dtype, int TR, cudaStream_t s) {
         const bool scaled = bw->key.precond != 0;
+        const bool blk = bw->key.precond == 2;
         const int nsys = (int)hs.size();
         std::vector<Sys> d(nsys);
         std::vector<int64_t> nf;
         layout_fwd(hs, TR, bw->hf, nf);
         bw->ha.assign(nsys + 1, 0);
         bw->hu.assign(nsys + 1, 0);
+        bw->hb.assign(nsys + 1, 0);
         for (int i = 0; i < nsys; ++i) {
             pdst_handle *h = hs[i];
             bw->ha[i + 1] = bw->ha[i] + round_up(h->n_adj, WPB);
             bw->hu[i + 1] = bw->hu[i] + round_up(((int64_t)h->n + LCOLS - 1) / LCOLS, WPB);
+            bw->hb[i + 1] = bw->hb[i] + ((int64_t)h->H + 1) / 2;   // two cells per warp item
         }
         bw->nf_items = bw->hf[nsys];
         bw->na_items = bw->ha[nsys];
         bw->nu_items = bw->hu[nsys];
+        bw->nb_items = bw->hb[nsys];
         const int device = hs[0]->device;
         bw->gi = bgrid(k_binit<VT, ST>, device, bw->nf_items);
         bw->gf = bgrid(k_bfwd<VT, ST>, device, bw->nf_items);
         bw->ga = bgrid(k_badj<VT, ST>, device, bw->na_items);
         bw->gu = bgrid(k_bupd<VT, ST>, device, bw->nu_items);
+        bw->gb = bgrid(k_bblk<VT, ST>, device, std::max<int64_t>(bw->nb_items, 1));
         const int64_t maxg = std::max(std::max(bw->gi, bw->gf), std::max(bw->ga, bw->gu));
         // (re)allocate vectors only on a new batch
         if (bw->bufs.empty()) {
@@ -934,6 +1036,7 @@ template <class VT, class ST> struct Batched {
             PDST_TRY(bw->adj_ctr.alloc(sizeof(unsigned)));
             PDST_TRY(bw->abeg.alloc(sizeof(int64_t) * (nsys + 1)));
             PDST_TRY(bw->ubeg.alloc(sizeof(int64_t) * (nsys + 1)));
+            PDST_TRY(bw->bbeg.alloc(sizeof(int64_t) * (nsys + 1)));
             PDST_CUDA(cudaMallocHost(&bw->h_active, sizeof(int) * nsys));
             PDST_CUDA(cudaMallocHost(&bw->h_scal, sizeof(LsqrScalars) * nsys * RMAX));
         }
@@ -962,7 +1065,10 @@ template <class VT, class ST> struct Batched {
             q.U = bw->bufs[NB * i]->as<ST>();
             q.V = bw->bufs[NB * i + 1]->as<ST>();
             q.Vs = scaled ? bw->bufs[NB * i + 7]->as<ST>() : q.V;
-            q.D = scaled ? h->colscale.as<double>() : nullptr;
+            q.D = (scaled && !blk) ? h->colscale.as<double>() : nullptr;
+            q.P = !blk ? nullptr
+                       : static_cast<const ST *>(sizeof(ST) == sizeof(double) ? h->blkP64.p
+                                                                              : h->blkP32.p);
             q.lamr = scaled ? 1 : 0;
             q.X = bw->bufs[NB * i + 2]->as<double>();
             q.W = bw->bufs[NB * i + 3]->as<double>();
@@ -982,6 +1088,8 @@ template <class VT, class ST> struct Batched {
         PDST_CUDA(cudaMemcpyAsync(bw->abeg.p, bw->ha.data(), sizeof(int64_t) * (nsys + 1),
                                   cudaMemcpyHostToDevice, s));
         PDST_CUDA(cudaMemcpyAsync(bw->ubeg.p, bw->hu.data(), sizeof(int64_t) * (nsys + 1),
+                                  cudaMemcpyHostToDevice, s));
+        PDST_CUDA(cudaMemcpyAsync(bw->bbeg.p, bw->hb.data(), sizeof(int64_t) * (nsys + 1),
                                   cudaMemcpyHostToDevice, s));
         PDST_CUDA(cudaStreamSynchronize(s));
         return PDST_OK;
@@ -1019,6 +1127,8 @@ template <class VT, class ST> struct Batched {
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gf * WPB), part, PH_FWD, act, ctr);
         k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part,
                                              ctr);
+        if (bw->key.precond == 2)
+            k_bblk<VT, ST><<<bw->gb, BT, 0, s>>>(sys, nsys, bw->bbeg.as<int64_t>(), bw->nb_items, 0);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
@@ -1034,6 +1144,8 @@ template <class VT, class ST> struct Batched {
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gi * WPB), part, PH_INIT, act, ctr);
         k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part,
                                              ctr);
+        if (bw->key.precond == 2)
+            k_bblk<VT, ST><<<bw->gb, BT, 0, s>>>(sys, nsys, bw->bbeg.as<int64_t>(), bw->nb_items, 1);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ_INIT, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
@@ -1103,7 +1215,8 @@ template <class VT, class ST> struct Batched {
         }
         PDST_TRY(load_inputs(bw, nsys, d_dev, init, s));
         PDST_TRY(start(bw, nsys, s));
-        launches += 6;
+        const int per_iter = bw->key.precond == 2 ? 7 : 6;
+        launches += per_iter;
         cudaGraphExec_t exec = nullptr;
         auto it = bw->graphs.find(kblock);
         if (it != bw->graphs.end()) {
@@ -1134,15 +1247,22 @@ template <class VT, class ST> struct Batched {
             for (int i = 0; i < nsys; ++i) any += bw->h_active[i];
             if (!any) break;
             PDST_CUDA(cudaGraphLaunch(exec, s));
-            launches += 6 * kblock;
+            launches += per_iter * kblock;
         }
         for (int i = 0; i < nsys; ++i) {
             const int64_t n = hs[i]->n;
             const unsigned g = (unsigned)std::max<int64_t>(
                 1, std::min<int64_t>((n * nrhs[i] + BT - 1) / BT, (int64_t)num_sms(device) * 8));
-            k_bfinal<<<g, BT, 0, s>>>(n, nrhs[i],
-                                      bw->key.precond ? hs[i]->colscale.as<double>() : nullptr,
-                                      bw->bufs[NB * i + 2]->as<double>(), m_out[i]);
+            if (bw->key.precond == 2)
+                k_bfinal_blk<ST><<<g, BT, 0, s>>>(
+                    n, hs[i]->nz, nrhs[i],
+                    static_cast<const ST *>(sizeof(ST) == sizeof(double) ? hs[i]->blkP64.p
+                                                                         : hs[i]->blkP32.p),
+                    bw->bufs[NB * i + 2]->as<double>(), m_out[i]);
+            else
+                k_bfinal<<<g, BT, 0, s>>>(n, nrhs[i],
+                                          bw->key.precond ? hs[i]->colscale.as<double>() : nullptr,
+                                          bw->bufs[NB * i + 2]->as<double>(), m_out[i]);
         }
         PDST_CUDA(cudaGetLastError());
         launches += nsys;
@@ -1208,15 +1328,19 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
     pdst_batched_opts_default(&local);
     if (opts) local = *opts;
     const int kblock = local.kblock > 0 ? local.kblock : 8;
-    PDST_CHECK_ARG(local.precond == 0 || local.precond == 1,
+    PDST_CHECK_ARG(local.precond >= 0 && local.precond <= 2,
                    "pdst_lsqr_batched: unknown precond %d", local.precond);
-    if (local.precond)
-        for (int i = 0; i < nsys; ++i)
-            if (!hs[i]->has_colscale) {
-                set_error("pdst_lsqr_batched: precond = 1 needs pdst_set_col_scaling on handle %d",
-                          i);
-                return PDST_ERR_STATE;
-            }
+    for (int i = 0; i < nsys; ++i) {
+        if (local.precond == 1 && !hs[i]->has_colscale) {
+            set_error("pdst_lsqr_batched: precond = 1 needs pdst_set_col_scaling on handle %d", i);
+            return PDST_ERR_STATE;
+        }
+        if (local.precond == 2 && !hs[i]->has_blkprec) {
+            set_error("pdst_lsqr_batched: precond = 2 needs pdst_set_block_precond on handle %d",
+                      i);
+            return PDST_ERR_STATE;
+        }
+    }
     PDST_CHECK_ARG(kblock <= 256, "pdst_lsqr_batched: kblock must be <= 256");
     PDST_CHECK_ARG(local.tile_rows >= 0 && local.tile_rows <= 4096,
                    "pdst_lsqr_batched: tile_rows out of range");

@@ -265,3 +265,99 @@ def test_scaled_batched_generic_paths_fixed_k_match_oracle(batch, k):
                               conlim=0, itmax=k, D=Dc, lam_rows=lams[j])
             assert inf[j]["iters"] == k
             assert rel(got[:, j], Dc * ref.x) < 1e-10, (p.nz, j, k)
+
+
+# ------------------------------------------ batched with the depth blocks
+# precond = 2: each system's handle blocks P (here the oracle's, so both sides
+# apply the same operator), pair (s, j) on [G P; w L P; lambda_j P] with no
+# recurrence damping, m = P y.  The blocks are those of the system's own
+# lambda; the other damping values of the batch are exact operator rows all
+# the same, so every pair keeps its own minimiser.
+
+def _set_oracle_blocks(b, hs):
+    from oracle import blockprec
+    Ps = []
+    for (p, G, GT, *_), h in zip(b, hs):
+        P = blockprec.block_precond(GT, (p.nx, p.ny, p.nz), p.w, p.lam)
+        h.set_block_precond(to_dev(P), p.w, p.lam)
+        Ps.append(P)
+    return Ps
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_block_batched_fixed_k_match_oracle(nzc, k):
+    """The 16-right-hand-side paths (nz = 8 and 16) and 13 right-hand sides."""
+    from oracle import blockprec
+    b, hs = nzc
+    Ps = _set_oracle_blocks(b, hs)
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    outs, infos, opts = pdst.lsqr_batched(hs, ds, [p.w for p, *_ in b], [l for *_, l in b], k,
+                                          0.0, dtype="f64", tile_rows=8, precond=2)
+    for (p, G, GT, D, lams), P, mo, inf in zip(b, Ps, outs, infos):
+        got = mo.cpu().numpy()
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k, P=P, lam_rows=lams[j])
+            assert inf[j]["iters"] == k
+            assert rel(got[:, j], blockprec.apply_blocks(P, ref.x)) < 1e-10, (p.nz, j, k)
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_block_batched_generic_paths_fixed_k_match_oracle(batch, k):
+    """Row stride 4 or 16 with nz = 8, 4 and 3 (the any-nz adjoint), FP64 and
+    FP32 (the FP32 bar is the FP32 single-system one)."""
+    from oracle import blockprec
+    b, hs = batch
+    Ps = []
+    for (p, G, D, lams), h in zip(b, hs):
+        GT = oracle.transpose(G)
+        P = blockprec.block_precond(GT, (p.nx, p.ny, p.nz), p.w, p.lam)
+        h.set_block_precond(to_dev(P), p.w, p.lam)
+        Ps.append((GT, P))
+    ds = [to_dev(D) for _, _, D, _ in b]
+    for dt, bar in (("f64", 1e-10), ("f32", 1e-4)):
+        outs, infos, _ = pdst.lsqr_batched(hs, ds, [p.w for p, _, _, _ in b],
+                                           [l for _, _, _, l in b], k, 0.0, dtype=dt,
+                                           tile_rows=4, precond=2)
+        for (p, G, D, lams), (GT, P), mo, inf in zip(b, Ps, outs, infos):
+            got = mo.cpu().numpy()
+            for j in range(D.shape[1]):
+                ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, D[:, j], atol=0, btol=0,
+                                  conlim=0, itmax=k, P=P, lam_rows=lams[j])
+                assert inf[j]["iters"] == k
+                assert rel(got[:, j], blockprec.apply_blocks(P, ref.x)) < bar, (dt, p.nz, j, k)
+
+
+def test_block_batched_converges_to_the_minimiser_in_fewer_iterations(nzc):
+    """FP32 batched with the device's own blocks against the oracle's
+    unpreconditioned tol-1e-12 solutions, in fewer iterations than the
+    column-norm form; precond = 2 without blocks is refused."""
+    b, hs = nzc
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    w = [p.w for p, *_ in b]
+    lams = [l for *_, l in b]
+    for (p, *_), h in zip(b, hs):
+        h.set_block_precond(None, p.w, p.lam)
+    o_b, i_b, opts = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32", precond=2)
+    _set_oracle_scaling(b, hs)
+    o_c, i_c, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32", precond=1)
+    it_b = sum(inf["iters"] for row in i_b for inf in row)
+    it_c = sum(inf["iters"] for row in i_c for inf in row)
+    print(f"FP32 batched, tol 1e-6: depth blocks {it_b} iterations, column norms {it_c}")
+    assert it_b < it_c
+    from oracle import blockprec
+    for (p, G, GT, D, lj), mb, inf in zip(b, o_b, i_b):
+        grid = (p.nx, p.ny, p.nz)
+        P = blockprec.block_precond(GT, grid, p.w, p.lam)
+        for j in (0, D.shape[1] // 2, D.shape[1] - 1):
+            ref = oracle.lsqr(G, GT, grid, p.w, lj[j], D[:, j], atol=1e-12, btol=1e-12,
+                              itmax=50000)
+            same = oracle.lsqr(G, GT, grid, p.w, 0.0, D[:, j], atol=1e-6, btol=1e-6,
+                               itmax=50000, P=P, lam_rows=lj[j])
+            assert inf[j]["istop"] in (1, 2)
+            e32 = rel(mb[:, j].cpu().numpy(), ref.x)
+            e_or = rel(blockprec.apply_blocks(P, same.x), ref.x)
+            assert e32 <= 2.0 * e_or + 1e-3, (p.nz, j, e32, e_or)
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
+        fresh = pdst.build_G_problem(b[0][0], dtypes=("f32",), formats=("blocked",))
+        pdst.lsqr_batched([fresh], [ds[0]], [1.0], [lams[0]], 10, 1e-6, dtype="f32", precond=2)
