@@ -60,6 +60,7 @@ FORMS = {
     "bf16-blocked-colnorm": ("bf16", "blocked", 1),
     "f32-blocked-learned": ("f32", "blocked", 2),
     "f32-blocked-block": ("f32", "blocked", 3),
+    "bf16-blocked-block": ("bf16", "blocked", 3),
     "f64-blocked-block": ("f64", "blocked", 3),
 }
 LIB_PRECOND = {0: 0, 1: 1, 2: 1, 3: 2}   # scaling code of FORMS -> pdst_lsqr_opts.precond

@@ -121,6 +121,22 @@ def test_outer_loop_fp32_scaled_inner_solves(sysm):
     assert np.max(np.abs(hist - ref.rms) / np.array(ref.rms)) < 1e-4
 
 
+def test_outer_loop_fp32_block_preconditioned_inner_solves(sysm):
+    """The benchmark's form inside the loop: the depth blocks of every rebuilt G
+    (precond = 2), FP32 values, two-phase refinement; the same model as the
+    FP64 oracle loop within the parity bar."""
+    p, m_true, d_obs, h = sysm
+    ref = outer.outer_loop(p, d_obs, p.w, p.lam, itmax=5000, tol=1e-10, max_outer=4,
+                           rms_tol=0.0, min_decrease=0.0)
+    m, hist, info = h.outer_loop(to_dev(d_obs), p.periods_s, p.w, p.lam, 5000, 1e-6,
+                                 max_outer=4, rms_tol=0.0, min_decrease=0.0, dtype="f32",
+                                 fmt="blocked", precond=2, refine=3, refine_dtype="f32",
+                                 refine_tol=1e-10)
+    assert info["updates"] == 4
+    assert rel(m.cpu().numpy(), ref.m) < 1e-4
+    assert np.max(np.abs(hist - ref.rms) / np.array(ref.rms)) < 1e-4
+
+
 def test_outer_loop_stopping_and_errors(sysm):
     p, m_true, d_obs, h = sysm
     m, hist, info = h.outer_loop(to_dev(d_obs), p.periods_s, p.w, p.lam, 100, 1e-8,
