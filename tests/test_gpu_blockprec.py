@@ -193,3 +193,27 @@ def test_mid_two_phase_block_form_matches_oracle_mref(mid):
     print(f"mid block two-phase: {e:.2e} ({two.info['sweeps']} sweeps, {two.info['iters']} it)")
     assert e <= 1e-4
     assert abs(r2 - r_ref) / r_ref <= 1e-6
+
+
+def test_empty_cells_and_zero_damping():
+    """Most cells crossed by no ray and lambda = 0 (no lambda rows): the
+    device's blocks equal the oracle's and the FP64 and two-phase FP32 block
+    solves reach the oracle's tol-1e-12 solution."""
+    require_cuda()
+    p = synth.custom(12, 12, 4, 3, 2, bend=0.0, seed=5, w=1.0, lam=0.0)
+    G, GT, d, h = _system(p)
+    grid = (p.nx, p.ny, p.nz)
+    B_ref = blockprec.depth_blocks(GT, grid, p.w, 0.0)
+    B = h.depth_blocks(p.w, 0.0).cpu().numpy()
+    scale = np.abs(B_ref).reshape(len(B_ref), -1).max(axis=1)[:, None, None]
+    assert np.max(np.abs(B - B_ref) / scale) < 1e-13
+    ref = oracle.lsqr(G, GT, grid, p.w, 0.0, d, atol=1e-12, btol=1e-12, itmax=50000)
+    h.set_block_precond(None, p.w, 0.0)
+    dd = to_dev(d)
+    r64 = h.lsqr(dd, p.w, 0.0, 20000, 1e-11, dtype="f64", fmt="blocked", precond=2)
+    assert r64.info["istop"] in (1, 2)
+    assert rel(r64.m.cpu().numpy(), ref.x) < 1e-7
+    two = h.lsqr(dd, p.w, 0.0, 20000, 1e-6, dtype="f32", fmt="blocked", precond=2, refine=3,
+                 refine_dtype="f32", refine_tol=1e-10)
+    assert rel(two.m.cpu().numpy(), ref.x) < 1e-6
+    h.close()

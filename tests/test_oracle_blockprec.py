@@ -119,3 +119,26 @@ def test_single_depth_blocks_equal_column_norm_scaling():
     b = oracle.lsqr(G, GT, grid, p.w, 0.0, d, atol=0, btol=0, conlim=0, itmax=25, D=D,
                     lam_rows=p.lam)
     np.testing.assert_allclose(a.x, b.x, rtol=1e-10, atol=1e-14)
+
+
+def test_blocks_definite_without_rays_or_damping():
+    """Cells that no ray crosses, and lambda = 0: with w > 0 every block is still
+    positive definite (a proper subset of the Laplacian's columns is linearly
+    independent: its only null vector is the constant one), and the
+    preconditioned LSQR still reaches the dense-QR minimiser."""
+    p = synth.custom(12, 12, 4, 3, 2, bend=0.0, seed=5, w=1.0, lam=0.0)
+    G = oracle.build_G_problem(p)
+    GT = oracle.transpose(G)
+    d = oracle.rhs_for(p, G)
+    grid = (p.nx, p.ny, p.nz)
+    cnt = np.diff(GT.ptr).reshape(p.nx * p.ny, p.nz).sum(axis=1)
+    assert (cnt == 0).sum() > 50                               # most cells see no ray
+    B = blockprec.depth_blocks(GT, grid, p.w, 0.0)
+    assert np.all(np.linalg.eigvalsh(B) > 1e-3)
+    P = blockprec.inverse_cholesky(B)
+    A = augmented_dense(p, G, p.w, 0.0)[: G.n_rows + p.n]     # no damping rows
+    b = np.concatenate([d, np.zeros(p.n)])
+    m_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    res = oracle.lsqr(G, GT, grid, p.w, 0.0, d, atol=1e-12, btol=1e-12, itmax=20000, P=P)
+    m = blockprec.apply_blocks(P, res.x)
+    assert np.linalg.norm(m - m_ls) / np.linalg.norm(m_ls) < 1e-6
