@@ -301,12 +301,11 @@ __device__ __forceinline__ AT blk_row_pairs_rt(const VT *__restrict__ vrow,
 // pairs in flight (32 bytes) leave the stream latency-bound.  FP32 and BF16
 // sums only: with FP64 sums the groups do not fit the registers (one group in
 // flight measured 1.3x slower than pairs).
-template <class VT, class AT, class XT>
+template <class VT, class AT, class XT, int US = 3>
 __device__ __forceinline__ AT blk_row_sextets(const VT *__restrict__ vrow,
                                               const XT *__restrict__ x,
                                               const int32_t *__restrict__ cells_row,
                                               uint32_t nrun, uint32_t nz, int hl) {
-    constexpr int US = 3;
     const uint32_t q = nz / 6u, ng = nrun * q;
     const DivQ dq(q);
     AT s = 0;
@@ -347,7 +346,7 @@ __device__ __forceinline__ AT blk_row_sextets(const VT *__restrict__ vrow,
     return s;
 }
 
-template <class VT, class ST, int Q>
+template <class VT, class ST, int Q, int SX = 3>
 __device__ __forceinline__ double fwd_rows_halfwarp(const OpArgs<VT, ST> &a, ST ia, ST cu,
                                                     int64_t gw, int64_t nw, int lane) {
     using AT = ST;
@@ -399,8 +398,9 @@ __device__ __forceinline__ double fwd_rows_halfwarp(const OpArgs<VT, ST> &a, ST 
                 part = blk_row_quads_rt<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc,
                                                     a.row_cells + e0, (uint32_t)(e1 - e0), nz, hl);
             else if (Q == -6)
-                part = blk_row_sextets<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc,
-                                                   a.row_cells + e0, (uint32_t)(e1 - e0), nz, hl);
+                part = blk_row_sextets<VT, AT, ST, SX>(a.val + e0 * (int64_t)nz, a.vsc,
+                                                       a.row_cells + e0, (uint32_t)(e1 - e0), nz,
+                                                       hl);
             else
                 part = blk_row_pairs_rt<VT, AT, ST>(a.val + e0 * (int64_t)nz, a.vsc,
                                                     a.row_cells + e0, (uint32_t)(e1 - e0), nz, hl);
@@ -495,15 +495,14 @@ __device__ __forceinline__ double adj_finish(const OpArgs<VT, ST> &a, int64_t j,
 // t = P_h^T s, v-bar_h <- t / beta - (beta/alpha) v-bar_h, and the forward's
 // input P_h v-bar_h; both products by shuffles over the cell's lanes, their
 // block entries read row by row (P_h for t, P_h^T for P_h v: each read of a
-// row is one contiguous segment across the lanes), eight at a time.  With
+// row is one contiguous segment across the lanes), CH at a time.  With
 // nz <= 16 the two half-warps each take half of every sum's terms and add
 // the halves with one shuffle.  Returns this lane's v-bar^2.
-template <class VT, class ST>
-__device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_t h, ST dot,
-                                                 ST ib, ST cv, ST wsm, ST lamr, int init,
-                                                 int lane) {
+template <int CH, class VT, class ST>
+__device__ __forceinline__ double adj_finish_blk_ch(const OpArgs<VT, ST> &a, int64_t h, ST dot,
+                                                    ST ib, ST cv, ST wsm, ST lamr, int init,
+                                                    int lane) {
     using AT = ST;
-    constexpr int CH = 8;
     const int nz = a.nz;
     const bool split = nz <= 16;
     const int k = split ? (lane & 15) : lane;     // the output depth this lane sums for
@@ -552,6 +551,16 @@ __device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_
     if (split) q += __shfl_xor_sync(FULL, q, 16);
     if (own) a.vsc[j] = q;
     return (double)v * (double)v;
+}
+
+// Batches of eight terms: with nz <= 16 one per half-warp and product.
+// Batches of sixteen for nz in 17..32 measured no faster (18 depth nodes);
+// batches of 32 made the kernel spill.
+template <class VT, class ST>
+__device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_t h, ST dot,
+                                                 ST ib, ST cv, ST wsm, ST lamr, int init,
+                                                 int lane) {
+    return adj_finish_blk_ch<8>(a, h, dot, ib, cv, wsm, lamr, init, lane);
 }
 
 // G^T rows of the adjoint sweep in the blocked CSC layout.  Work item = a
@@ -874,7 +883,12 @@ __global__ void __launch_bounds__(LT) k_step_sweep(const LsqrScalars *base, cons
 
 // u-bar <- (A v-bar)/alpha - (alpha/beta) u-bar;  beta <- ||u-bar||.  BF16
 // values: three blocks per SM, as in the adjoint.
-template <class VT, class ST, int FMT, int MB = (sizeof(VT) == 2 ? 3 : 4)>
+// PATH 6: a kernel of its own for the six-entry groups (nz % 6 == 0 off the
+// quads, FP32 values), with two groups in flight instead of three (2.3 %
+// faster on 18 depth nodes).  The generic kernel keeps the path too: without
+// it the quads of 4 measured 9 % slower (a different schedule, although the
+// generic kernel then no longer spilled).
+template <class VT, class ST, int FMT, int MB = (sizeof(VT) == 2 ? 3 : 4), int PATH = 0>
 __global__ void __launch_bounds__(LT, MB) k_fwd(OpArgs<VT, ST> a) {
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
@@ -890,7 +904,10 @@ __global__ void __launch_bounds__(LT, MB) k_fwd(OpArgs<VT, ST> a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double ss = 0.0;
     if constexpr (FMT == FMT_BLK) {
-        ss = fwd_rows_blk<VT, ST>(a, ia, cu, gw, nw, lane);
+        if constexpr (PATH == 6)
+            ss = fwd_rows_halfwarp<VT, ST, -6, 2>(a, ia, cu, gw, nw, lane);
+        else
+            ss = fwd_rows_blk<VT, ST>(a, ia, cu, gw, nw, lane);
     } else {
         for (int64_t r = gw; r < a.m; r += nw) {
             AT dot = dot_elem<VT, AT, ST>(a.row_ptr, a.col, a.val, a.vsc, r, lane);
@@ -1445,6 +1462,7 @@ __host__ __device__ constexpr bool fwd_three_blocks(int nz) {
 }
 template <class VT, class ST, int FMT> static auto fwd_kernel(int nz) {
     if constexpr (FMT == FMT_BLK && sizeof(VT) == 4 && sizeof(ST) == 4) {
+        if ((nz & 3) != 0 && nz % 6 == 0) return k_fwd<VT, ST, FMT, 4, 6>;
         if (fwd_three_blocks(nz)) return k_fwd<VT, ST, FMT, 3>;
     }
     return k_fwd<VT, ST, FMT>;
