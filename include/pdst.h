@@ -374,7 +374,9 @@ void pdst_batched_opts_default(pdst_batched_opts *o);
  * w[s]: smoothing weight per system.  lambda[s]: nrhs[s] damping values (host).
  * m_out_dev[s]: n_s x nrhs[s] FP64 (device, caller-owned), right-hand side
  * fastest.  infos: sum(nrhs) entries, system-major (may be NULL).  Each
- * system needs nz <= 16 (PDST_ERR_LIMIT otherwise).  dtype:
+ * system needs nz <= 32 (PDST_ERR_LIMIT otherwise); a batch with a system of
+ * more than 16 depth nodes runs its adjoint in kernels that hold 32 depths
+ * per lane (two blocks per SM) for all of its systems.  dtype:
  * values and u/v vectors (PDST_F32 / PDST_BF16 use FP32 vectors).  opts may be
  * NULL (autotuned tile, kblock 8); its out fields are filled when given.
  * Work space for the batch is allocated on the first call and reused while the

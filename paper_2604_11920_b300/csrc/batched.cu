@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(BT, 4) k_bfwd(BSys<VT, ST> *sys, int nsys, con
     ws.finish(partial, nsys, gw, nw);
 }
 
-constexpr int BNZ = 16;   // depths per cell handled in registers by the adjoint
+constexpr int BNZ = 16;   // depths per cell held in registers by the adjoint's generic path
+constexpr int BNZ_WIDE = 32;   // the same in the kernels of batches with deeper systems
 
 // Laplacian of column jc for right-hand sides 4g..4g+3 of a block stored with
 // row stride 16 (same neighbour order as laplace_strided).
@@ -557,9 +558,10 @@ __device__ __forceinline__ double adj_item16(const BSys<VT, ST> &S, int64_t li, 
 // half-warps take alternate rows; each row's index and u are read once and its
 // nz values as nz/4 16-byte vectors (blocked CSC).  Lanes j of the first half
 // return the sum of squares of the new v for right-hand side j.
-template <class VT, class ST>
+template <int W, class VT, class ST>
 __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li, int init, int lane,
                                                int *flag) {
+    constexpr int BNZ = W;
     using AT = ST;
     const int j = lane & 15, half = lane >> 4;
     const int R = S.R, RS = S.RS, nz = S.nz;
@@ -658,10 +660,12 @@ __device__ __forceinline__ double adj_item_any(const BSys<VT, ST> &S, int64_t li
 // Items are drawn dynamically from a counter (reset by k_bred), one ahead;
 // every cell's sums go to its slots, so the result does not depend on which
 // warp took which item.  The per-warp partial slots stay zero.
-template <class VT, class ST>
-__global__ void __launch_bounds__(BT, 4) k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
-                                             int64_t nitems, int init, double *partial,
-                                             unsigned *next_item) {
+// W = BNZ_WIDE: the kernel of batches with a system of more than BNZ depths
+// (its generic path holds 32 depths per lane, two blocks per SM).
+template <class VT, class ST, int W = BNZ>
+__global__ void __launch_bounds__(BT, W == BNZ ? 4 : 2)
+    k_badj(BSys<VT, ST> *sys, int nsys, const int64_t *beg, int64_t nitems, int init,
+           double *partial, unsigned *next_item) {
     __shared__ int last_flag[WPB];
     WarpSum ws;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -679,8 +683,10 @@ __global__ void __launch_bounds__(BT, 4) k_badj(BSys<VT, ST> *sys, int nsys, con
                 adj_item16<16>(S, li, init, lane, last_flag + warp);
             else if (S.RS == 16 && S.nz == 8)
                 adj_item16<8>(S, li, init, lane, last_flag + warp);
+            else if (W == BNZ || S.nz <= BNZ)
+                adj_item_any<BNZ>(S, li, init, lane, last_flag + warp);
             else
-                adj_item_any(S, li, init, lane, last_flag + warp);
+                adj_item_any<W>(S, li, init, lane, last_flag + warp);
         }
     }
     ws.finish(partial, nsys, gw, nw);
@@ -760,7 +766,7 @@ __global__ void k_bfinal_blk(int64_t n, int nz, int R, const ST *__restrict__ P,
 // v-bar (start step: t / beta), Vs = P_h v-bar; the cell's sum of v-bar^2 per
 // right-hand side goes to its slot (added in cell order by k_bred).  The
 // blocks are read once per cell and broadcast to the lanes.
-template <class VT, class ST>
+template <class VT, class ST, int BNZ = pdst::BNZ>
 __global__ void __launch_bounds__(BT) k_bblk(BSys<VT, ST> *sys, int nsys, const int64_t *beg,
                                              int64_t nitems, int init) {
     using AT = ST;
@@ -922,6 +928,7 @@ struct BatchWork {
     BatchKey key;
     int TR = 0;
     bool tuned = false;
+    bool wide = false;   // a system has more than BNZ depths: the W = BNZ_WIDE kernels
     std::vector<DevBuf *> bufs;
     DevBuf desc, scal, partial, fbeg, abeg, ubeg, bbeg, active, adj_ctr;
     int *h_active = nullptr;
@@ -998,9 +1005,14 @@ template <class VT, class ST> struct Batched {
         const int device = hs[0]->device;
         bw->gi = bgrid(k_binit<VT, ST>, device, bw->nf_items);
         bw->gf = bgrid(k_bfwd<VT, ST>, device, bw->nf_items);
-        bw->ga = bgrid(k_badj<VT, ST>, device, bw->na_items);
+        int maxnz = 0;
+        for (auto *h : hs) maxnz = std::max(maxnz, (int)h->nz);
+        bw->wide = maxnz > BNZ;
+        bw->ga = bw->wide ? bgrid(k_badj<VT, ST, BNZ_WIDE>, device, bw->na_items)
+                          : bgrid(k_badj<VT, ST>, device, bw->na_items);
         bw->gu = bgrid(k_bupd<VT, ST>, device, bw->nu_items);
-        bw->gb = bgrid(k_bblk<VT, ST>, device, std::max<int64_t>(bw->nb_items, 1));
+        bw->gb = bw->wide ? bgrid(k_bblk<VT, ST, BNZ_WIDE>, device, std::max<int64_t>(bw->nb_items, 1))
+                          : bgrid(k_bblk<VT, ST>, device, std::max<int64_t>(bw->nb_items, 1));
         const int64_t maxg = std::max(std::max(bw->gi, bw->gf), std::max(bw->ga, bw->gu));
         // (re)allocate vectors only on a new batch
         if (bw->bufs.empty()) {
@@ -1117,6 +1129,26 @@ template <class VT, class ST> struct Batched {
         return PDST_OK;
     }
 
+    // The adjoint phase (and, with depth blocks, the cells' finish) in the
+    // kernels of the batch's width.
+    static void launch_adj(BatchWork *bw, int nsys, int init, cudaStream_t s) {
+        Sys *sys = bw->desc.as<Sys>();
+        double *part = bw->partial.as<double>();
+        unsigned *ctr = bw->adj_ctr.as<unsigned>();
+        const int64_t *ab = bw->abeg.as<int64_t>(), *bb = bw->bbeg.as<int64_t>();
+        if (bw->wide)
+            k_badj<VT, ST, BNZ_WIDE><<<bw->ga, BT, 0, s>>>(sys, nsys, ab, bw->na_items, init, part,
+                                                          ctr);
+        else
+            k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, ab, bw->na_items, init, part, ctr);
+        if (bw->key.precond == 2) {
+            if (bw->wide)
+                k_bblk<VT, ST, BNZ_WIDE><<<bw->gb, BT, 0, s>>>(sys, nsys, bb, bw->nb_items, init);
+            else
+                k_bblk<VT, ST><<<bw->gb, BT, 0, s>>>(sys, nsys, bb, bw->nb_items, init);
+        }
+    }
+
     static void launch_iter(BatchWork *bw, int nsys, cudaStream_t s) {
         Sys *sys = bw->desc.as<Sys>();
         double *part = bw->partial.as<double>();
@@ -1125,10 +1157,7 @@ template <class VT, class ST> struct Batched {
         k_bfwd<VT, ST><<<bw->gf, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
                                              part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gf * WPB), part, PH_FWD, act, ctr);
-        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 0, part,
-                                             ctr);
-        if (bw->key.precond == 2)
-            k_bblk<VT, ST><<<bw->gb, BT, 0, s>>>(sys, nsys, bw->bbeg.as<int64_t>(), bw->nb_items, 0);
+        launch_adj(bw, nsys, 0, s);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
@@ -1142,10 +1171,7 @@ template <class VT, class ST> struct Batched {
         k_binit<VT, ST><<<bw->gi, BT, 0, s>>>(sys, nsys, bw->fbeg.as<int64_t>(), bw->nf_items, bw->TR,
                                               part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gi * WPB), part, PH_INIT, act, ctr);
-        k_badj<VT, ST><<<bw->ga, BT, 0, s>>>(sys, nsys, bw->abeg.as<int64_t>(), bw->na_items, 1, part,
-                                             ctr);
-        if (bw->key.precond == 2)
-            k_bblk<VT, ST><<<bw->gb, BT, 0, s>>>(sys, nsys, bw->bbeg.as<int64_t>(), bw->nb_items, 1);
+        launch_adj(bw, nsys, 1, s);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->ga * WPB), part, PH_ADJ_INIT, act, ctr);
         k_bupd<VT, ST><<<bw->gu, BT, 0, s>>>(sys, nsys, bw->ubeg.as<int64_t>(), bw->nu_items, part);
         k_bred<VT, ST><<<nsys, RED_T, 0, s>>>(sys, (int)(bw->gu * WPB), part, PH_UPD, act, ctr);
@@ -1317,9 +1343,9 @@ extern "C" pdst_status pdst_lsqr_batched(int32_t nsys, const pdst_handle_t *hs, 
             set_error("pdst_lsqr_batched: values of dtype %d were not kept in handle %d", dtype, i);
             return PDST_ERR_STATE;
         }
-        if (hs[i]->nz > BNZ) {
+        if (hs[i]->nz > BNZ_WIDE) {
             set_error("pdst_lsqr_batched: nz = %d in handle %d; the batched form supports nz <= %d",
-                      hs[i]->nz, i, BNZ);
+                      hs[i]->nz, i, BNZ_WIDE);
             return PDST_ERR_LIMIT;
         }
         H[i] = hs[i];

@@ -361,3 +361,95 @@ def test_block_batched_converges_to_the_minimiser_in_fewer_iterations(nzc):
     with pytest.raises(pdst.PdstError, match="PDST_ERR_STATE"):
         fresh = pdst.build_G_problem(b[0][0], dtypes=("f32",), formats=("blocked",))
         pdst.lsqr_batched([fresh], [ds[0]], [1.0], [lams[0]], 10, 1e-6, dtype="f32", precond=2)
+
+
+# ------------------------------------------------ deeper systems (nz > 16)
+# A batch with a system of more than 16 depth nodes runs the adjoint kernels
+# that hold 32 depths per lane, for all of its systems.
+
+def wide_batch():
+    probs = [synth.custom(9, 8, 20, 12, 4, bend=0.15, seed=61, w=1.0, lam=0.1, dz_km=1.0),
+             synth.custom(10, 7, 8, 10, 3, bend=0.1, seed=62, w=2.0, lam=0.05),
+             synth.custom(6, 6, 27, 8, 3, bend=0.15, seed=63, w=0.5, lam=0.2, dz_km=1.0)]
+    nrhs = [16, 5, 3]
+    out = []
+    for p, R in zip(probs, nrhs):
+        G = oracle.build_G_problem(p)
+        cols, lams = [], []
+        for j in range(R):
+            m = synth.checkerboard(p.nx, p.ny, p.nz, 2 + (j % 5), 0.05) * (1 if j % 2 else -1)
+            cols.append(oracle.rhs_for(p, G, m_model=m, noise=synth.rhs_noise(p.seed, p.m_rows, j)))
+            lams.append(float(np.logspace(-3, 0, R)[j]) if R > 1 else p.lam)
+        out.append((p, G, oracle.transpose(G), np.stack(cols, axis=1), lams))
+    return out
+
+
+@pytest.fixture(scope="module")
+def wide():
+    require_cuda()
+    b = wide_batch()
+    hs = [pdst.build_G_problem(p, dtypes=("f64", "f32"), formats=("blocked",))
+          for p, *_ in b]
+    yield b, hs
+    for h in hs:
+        h.close()
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_wide_batch_fixed_k_match_oracle(wide, k):
+    """nz = 20, 8 and 27 in one batch: unscaled and with the oracle's depth
+    blocks, FP64, element by element against the oracle."""
+    from oracle import blockprec
+    b, hs = wide
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    w = [p.w for p, *_ in b]
+    lams = [l for *_, l in b]
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, w, lams, k, 0.0, dtype="f64", tile_rows=4)
+    for (p, G, GT, D, lj), mo, inf in zip(b, outs, infos):
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, lj[j], D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k)
+            assert inf[j]["iters"] == k
+            assert rel(mo[:, j].cpu().numpy(), ref.x) < 1e-10, (p.nz, j, k)
+    Ps = []
+    for (p, G, GT, *_), h in zip(b, hs):
+        P = blockprec.block_precond(GT, (p.nx, p.ny, p.nz), p.w, p.lam)
+        h.set_block_precond(to_dev(P), p.w, p.lam)
+        Ps.append(P)
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, w, lams, k, 0.0, dtype="f64", tile_rows=4,
+                                       precond=2)
+    for (p, G, GT, D, lj), P, mo, inf in zip(b, Ps, outs, infos):
+        for j in range(D.shape[1]):
+            ref = oracle.lsqr(G, GT, (p.nx, p.ny, p.nz), p.w, 0.0, D[:, j], atol=0, btol=0,
+                              conlim=0, itmax=k, P=P, lam_rows=lj[j])
+            assert rel(mo[:, j].cpu().numpy(), blockprec.apply_blocks(P, ref.x)) < 1e-10, \
+                (p.nz, j, k)
+
+
+def test_wide_batch_converged_fp32_and_limit(wide):
+    b, hs = wide
+    ds = [to_dev(D) for _, _, _, D, _ in b]
+    w = [p.w for p, *_ in b]
+    lams = [l for *_, l in b]
+    for (p, *_), h in zip(b, hs):
+        h.set_block_precond(None, p.w, p.lam)
+    outs, infos, _ = pdst.lsqr_batched(hs, ds, w, lams, 20000, 1e-6, dtype="f32", precond=2)
+    from oracle import blockprec
+    for (p, G, GT, D, lj), mo, inf in zip(b, outs, infos):
+        grid = (p.nx, p.ny, p.nz)
+        P = blockprec.block_precond(GT, grid, p.w, p.lam)
+        for j in (0, D.shape[1] - 1):
+            ref = oracle.lsqr(G, GT, grid, p.w, lj[j], D[:, j], atol=1e-12, btol=1e-12,
+                              itmax=50000)
+            same = oracle.lsqr(G, GT, grid, p.w, 0.0, D[:, j], atol=1e-6, btol=1e-6,
+                               itmax=50000, P=P, lam_rows=lj[j])
+            assert inf[j]["istop"] in (1, 2)
+            e32 = rel(mo[:, j].cpu().numpy(), ref.x)
+            e_or = rel(blockprec.apply_blocks(P, same.x), ref.x)
+            assert e32 <= 2.0 * e_or + 1e-3, (p.nz, j, e32, e_or)
+    deep = synth.custom(4, 4, 34, 6, 2, bend=0.0, seed=64)
+    hd = pdst.build_G_problem(deep, dtypes=("f32",), formats=("blocked",))
+    dd = to_dev(np.zeros((hd.m, 1)))
+    with pytest.raises(pdst.PdstError, match="PDST_ERR_LIMIT"):
+        pdst.lsqr_batched([hd], [dd], [1.0], [[0.1]], 10, 1e-6, dtype="f32")
+    hd.close()
