@@ -1,5 +1,6 @@
 """Evaluate the learned scaling on held-out systems against column-norm
-scaling and no scaling.
+scaling and no scaling, with the per-cell depth-block preconditioner beside
+them (the benchmark's chosen form).
 
 Per system: a tight reference solution (the training script's recipe), then
 (1) the accuracy-matched metric of the benchmark -- LSQR iterations and time of
@@ -45,17 +46,19 @@ def run_one(p, params):
             h.set_col_scaling_power(p.w, p.lam, 1.0)
         elif form == "learned":
             learned_scaling(h, p, params)
+        elif form == "blocks":
+            h.set_block_precond(None, p.w, p.lam)
 
-    for form in ("colnorm", "learned"):
+    for form, pc in (("colnorm", 1), ("learned", 1), ("blocks", 2)):
         set_form(form)
-        it, rt = accuracy_cost(h, p, d, m_ref)
+        it, rt = accuracy_cost(h, p, d, m_ref, precond=pc)
         acc = {"iters": it, "refine_tol": rt, "s": None, "model_error": None}
         if it is not None:
             set_form(form)   # the scaling is part of the timed step
-            r, t = timed(precond=1, refine=3, refine_dtype="f32", refine_tol=rt)
+            r, t = timed(precond=pc, refine=3, refine_dtype="f32", refine_tol=rt)
             acc.update(s=t, model_error=relerr(r.m, m_ref))
         out[f"acc_{form}"] = acc
-    for form, pc in (("none", 0), ("colnorm", 1), ("learned", 1)):
+    for form, pc in (("none", 0), ("colnorm", 1), ("learned", 1), ("blocks", 2)):
         set_form(form)
         r, t = timed(precond=pc)
         out[form] = {"iters": r.info["iters"], "istop": r.info["istop"], "s": t,
@@ -66,11 +69,11 @@ def run_one(p, params):
 
 def summarise(rows):
     s = {}
-    for key in ("none", "colnorm", "learned"):
+    for key in ("none", "colnorm", "learned", "blocks"):
         s[key] = {"mean_iters": float(np.mean([r[key]["iters"] for r in rows])),
                   "mean_s": float(np.mean([r[key]["s"] for r in rows])),
                   "mean_model_error": float(np.mean([r[key]["model_error"] for r in rows]))}
-    for key in ("acc_colnorm", "acc_learned"):
+    for key in ("acc_colnorm", "acc_learned", "acc_blocks"):
         ok = [r[key] for r in rows if r[key]["iters"] is not None]
         s[key] = {"reached": len(ok), "of": len(rows),
                   "mean_iters": float(np.mean([a["iters"] for a in ok])) if ok else None,

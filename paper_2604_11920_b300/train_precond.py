@@ -63,12 +63,12 @@ def relerr(a, b):
     return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
 
-def accuracy_cost(h, p, d, m_ref, cap=None):
+def accuracy_cost(h, p, d, m_ref, cap=None, precond=1):
     """LSQR iterations of the accuracy-matched two-phase solve with the handle's
-    current scaling (None if no rung of LADDER reaches TARGET_ERR, or if a rung
-    already needs more than `cap`)."""
+    current scaling (precond 1) or depth blocks (precond 2); None if no rung of
+    LADDER reaches TARGET_ERR, or if a rung already needs more than `cap`."""
     for rt in LADDER:
-        r = h.lsqr(d, p.w, p.lam, 200000, p.tol, dtype="f32", fmt="blocked", precond=1,
+        r = h.lsqr(d, p.w, p.lam, 200000, p.tol, dtype="f32", fmt="blocked", precond=precond,
                    refine=3, refine_dtype="f32", refine_tol=rt)
         if relerr(r.m, m_ref) <= TARGET_ERR:
             return r.info["iters"], rt

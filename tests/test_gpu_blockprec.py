@@ -217,3 +217,32 @@ def test_empty_cells_and_zero_damping():
                  refine_dtype="f32", refine_tol=1e-10)
     assert rel(two.m.cpu().numpy(), ref.x) < 1e-6
     h.close()
+
+
+@pytest.mark.parametrize("nz", [17, 18, 20, 32])
+def test_fixed_k_iterates_deep_columns(nz):
+    """Depth counts above 16 (the finish without the half-warp split; 18 and 20
+    are the paper-shaped and 100 x 100 x 20 systems' depth counts, 32 the
+    largest the blocks support): the device's blocks and, with the oracle's
+    blocks given to it, FP64 and FP32 iterates at a fixed k against the
+    oracle's."""
+    require_cuda()
+    p = synth.custom(7, 6, nz, 9, 3, bend=0.15, seed=70 + nz, w=1.0, lam=0.1, dz_km=1.0)
+    G, GT, d, h = _system(p)
+    grid = (p.nx, p.ny, p.nz)
+    B_ref = blockprec.depth_blocks(GT, grid, p.w, p.lam)
+    B = h.depth_blocks(p.w, p.lam).cpu().numpy()
+    scale = np.abs(B_ref).reshape(len(B_ref), -1).max(axis=1)[:, None, None]
+    assert np.max(np.abs(B - B_ref) / scale) < 1e-13
+    P = blockprec.inverse_cholesky(B_ref)
+    h.set_block_precond(to_dev(P), p.w, p.lam)
+    dd = to_dev(d)
+    for k in (1, 6):
+        ref = oracle.lsqr(G, GT, grid, p.w, 0.0, d, atol=0, btol=0, conlim=0, itmax=k, P=P,
+                          lam_rows=p.lam)
+        m_ref = blockprec.apply_blocks(P, ref.x)
+        for dt, bar in (("f64", 1e-10), ("f32", 1e-4)):
+            r = h.lsqr(dd, p.w, p.lam, k, 0.0, dtype=dt, fmt="blocked", precond=2, conlim=1e300)
+            assert r.info["iters"] == k
+            assert rel(r.m.cpu().numpy(), m_ref) < bar, (nz, k, dt)
+    h.close()
