@@ -556,10 +556,61 @@ __device__ __forceinline__ double adj_finish_blk_ch(const OpArgs<VT, ST> &a, int
 // Batches of eight terms: with nz <= 16 one per half-warp and product.
 // Batches of sixteen for nz in 17..32 measured no faster (18 depth nodes);
 // batches of 32 made the kernel spill.
+// nz <= 16 with every load of the lane issued before the first use: its
+// block entries for both products (at most eight each) and its old v-bar,
+// then the stencil terms; one round trip to L2 instead of three.
+template <class VT, class ST>
+__device__ __forceinline__ double adj_finish_blk16(const OpArgs<VT, ST> &a, int64_t h, ST dot,
+                                                   ST ib, ST cv, ST wsm, ST lamr, int init,
+                                                   int lane) {
+    using AT = ST;
+    const int nz = a.nz;
+    const int k = lane & 15;
+    const bool on = k < nz;
+    const bool own = lane < nz;
+    const int ih = (nz + 1) >> 1;
+    const int i0 = lane >= 16 ? ih : 0;
+    const int64_t j = h * nz + lane;
+    const ST *P = static_cast<const ST *>(a.Pb) + h * nz * nz;
+    const ST *PT = static_cast<const ST *>(a.PbT) + h * nz * nz;
+    AT p1[8], p2[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u;
+        const bool in = on && u < ih && i < nz;
+        p1[u] = (in && i <= k) ? (AT)P[i * nz + k] : (AT)0;
+        p2[u] = (in && i >= k) ? (AT)PT[i * nz + k] : (AT)0;
+    }
+    const AT vold = (own && !init) ? (AT)a.vbar[j] : (AT)0;
+    AT sj = 0;
+    if (own) {
+        sj = dot + wsm * laplace<AT, ST>(a.ubar + a.m, j, a.nx, a.ny, a.nz);
+        if (a.lam_rows_on) sj += lamr * (AT)a.ubar[a.m + a.n + j];
+    }
+    AT t = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += p1[u] * __shfl_sync(FULL, sj, (i0 + u) & 31);
+    t += __shfl_xor_sync(FULL, t, 16);
+    AT v = 0;
+    if (own) {
+        v = init ? t * ib : t * ib - cv * vold;
+        a.vbar[j] = v;
+    }
+    AT q = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q += p2[u] * __shfl_sync(FULL, v, (i0 + u) & 31);
+    q += __shfl_xor_sync(FULL, q, 16);
+    if (own) a.vsc[j] = q;
+    return (double)v * (double)v;
+}
+
 template <class VT, class ST>
 __device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_t h, ST dot,
                                                  ST ib, ST cv, ST wsm, ST lamr, int init,
                                                  int lane) {
+    if constexpr (sizeof(ST) == 4) {   // with 8-byte vectors the preloads spill
+        if (a.nz <= 16) return adj_finish_blk16(a, h, dot, ib, cv, wsm, lamr, init, lane);
+    }
     return adj_finish_blk_ch<8>(a, h, dot, ib, cv, wsm, lamr, init, lane);
 }
 
