@@ -358,6 +358,29 @@ def event_time(stream, fn):
     return e0.elapsed_time(e1) / 1e3, out
 
 
+def stream_ceiling(nbytes, stream, reps=5):
+    """Device time of one plain sequential read of `nbytes` (pdst_stream_read
+    over a buffer of that size, L2 flushed before each read by writing 256 MB):
+    the rate at which this GPU streams the sweep's value bytes with no gather
+    and no dependent load, the context for the sweeps' own fraction of peak."""
+    import torch
+
+    from paper_2604_11920_b300 import pdst
+    nbytes -= nbytes % 16
+    buf = torch.rand(nbytes // 4, device="cuda", dtype=torch.float32)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    best = None
+    for i in range(reps + 1):
+        flush.fill_(float(i))
+        t, _ = event_time(stream, lambda: pdst.stream_read(buf, stream))
+        if i > 0:
+            best = t if best is None else min(best, t)
+    del buf, flush
+    return {"what": "pdst_stream_read (16-byte streaming loads, 8 blocks per SM) over a "
+                    f"buffer of the sweep's value bytes, L2 flushed, best of {reps}",
+            "bytes": nbytes, "ms": best * 1e3, "gbs": nbytes / best / 1e9}
+
+
 def relerr_to(m_ref):
     import torch
 
@@ -572,6 +595,10 @@ def run_pdst(args, rank, world):
                        "avg_launch_ms": kms[dom], "other_sweep": {
                            "kernel": {"fwd": "k_adj", "adj": "k_fwd"}[dom],
                            "frac": chosen_roof["frac_of_hbm"]["adj" if dom == "fwd" else "fwd"]}}
+    sc = stream_ceiling(VALUE_BYTES[dtype] * h.nnz, stream)
+    sc["frac_of_peak"] = round(sc["gbs"] / peak, 4)
+    sc["sweep_frac_of_ceiling"] = round(achieved / sc["gbs"], 4)
+    out["roofline"]["stream_ceiling"] = sc
 
     # ---- end to end through the host entry point (pinned host d and m)
     e2e = None

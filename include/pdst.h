@@ -526,6 +526,17 @@ pdst_status pdst_outer_loop(pdst_handle_t h, const double *d_obs_dev, const doub
                             const pdst_outer_opts *opts, double *m_out_dev,
                             double *rms_hist_host, pdst_outer_info *info, void *stream);
 
+/*
+ * Measurement aid (no counterpart in the paper): one sequential read of
+ * `bytes` bytes at buf_dev (device, caller-owned, 16-byte aligned, bytes a
+ * multiple of 16) with 16-byte streaming loads by a grid of 8 blocks per SM,
+ * no gathers and no dependent loads; the data are summed so the loads are
+ * kept, and nothing is written.  Timed by the caller on `stream`, it gives the
+ * rate at which this GPU streams a sweep's value bytes, the ceiling against
+ * which the sweeps' gathers are read.  Asynchronous.  Errors: PDST_ERR_ARG.
+ */
+pdst_status pdst_stream_read(const void *buf_dev, int64_t bytes, void *stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdst_last_error_string(void);
 

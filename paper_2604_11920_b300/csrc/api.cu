@@ -166,3 +166,34 @@ extern "C" pdst_status pdst_G_export_csc(pdst_handle_t h, int32_t dtype, int64_t
     }
     return PDST_OK;
 }
+
+namespace pdst {
+
+// Sequential float4 read of a buffer (pdst_stream_read); the sum is compared
+// with a value it never takes, so the loads stay and nothing is stored.
+__global__ void __launch_bounds__(256) k_stream_read(const float4 *__restrict__ p, int64_t n4,
+                                                     float *never) {
+    float s = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 t = __ldcs(p + i);
+        s += (t.x + t.y) + (t.z + t.w);
+    }
+    if (s == -1.2345e-37f && never) *never = s;
+}
+
+}  // namespace pdst
+
+extern "C" pdst_status pdst_stream_read(const void *buf_dev, int64_t bytes, void *stream) {
+    using namespace pdst;
+    PDST_CHECK_ARG(buf_dev != nullptr, "pdst_stream_read: buffer is NULL");
+    PDST_CHECK_ARG(bytes >= 0 && bytes % 16 == 0, "pdst_stream_read: bytes must be a multiple of 16");
+    PDST_CHECK_ARG(reinterpret_cast<uintptr_t>(buf_dev) % 16 == 0,
+                   "pdst_stream_read: buffer must be 16-byte aligned");
+    int dev = 0;
+    PDST_CUDA(cudaGetDevice(&dev));
+    k_stream_read<<<num_sms(dev) * 8, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float4 *>(buf_dev), bytes / 16, nullptr);
+    PDST_CUDA(cudaGetLastError());
+    return PDST_OK;
+}

@@ -135,6 +135,7 @@ SIGNATURES = {
     "pdst_outer_opts_default": (None, [ctypes.POINTER(OuterOpts)]),
     "pdst_outer_loop": (_i32, [_vp, _vp, _vp, _d, _d, _i32, _d, ctypes.POINTER(OuterOpts), _vp,
                                _vp, ctypes.POINTER(OuterInfo), _vp]),
+    "pdst_stream_read": (_i32, [_vp, _i64, _vp]),
     "pdst_last_error_string": (ctypes.c_char_p, []),
     "pdst_version": (_i32, []),
 }
@@ -184,6 +185,13 @@ def _dev_ptr(t, numel=None, dtype=None, name="tensor"):
 
 def _np_ptr(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def stream_read(buf, stream=None):
+    """pdst_stream_read: one sequential read of a CUDA tensor's bytes (a
+    measurement aid: the streaming ceiling beside the sweeps' rates)."""
+    nbytes = buf.numel() * buf.element_size()
+    _check(load().pdst_stream_read(ctypes.c_void_p(buf.data_ptr()), nbytes, _stream(stream)))
 
 
 def lsqr_opts(dtype="f64", fmt="element", atol=-1.0, btol=-1.0, conlim=0.0, precond=0,
