@@ -81,6 +81,19 @@ template <class VT, class ST> struct OpArgs {
     LsqrSync *sy;
 };
 
+// ---------------------------------------------- programmatic dependent launch
+
+// The sweeps of an iteration are launched with programmatic stream
+// serialisation: a kernel's blocks may be scheduled while the kernel before it
+// is still finishing (its last block's fixed-order sums), and wait here until
+// that kernel has completed and its writes are visible.  Without the launch
+// attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel's blocks be scheduled as this kernel's blocks leave.
+__device__ __forceinline__ void pdl_allow_next() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------ dot products
 
 // sum_p val[p] * x[idx[p]] over p in [ptr[r], ptr[r+1]) by one warp: ragged
@@ -626,7 +639,7 @@ __device__ __forceinline__ double adj_finish_blk(const OpArgs<VT, ST> &a, int64_
 template <class VT, class ST, int G>
 __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST ib, ST cv, ST wsm,
                                                     ST lamr, int init, int64_t gw, int64_t nw,
-                                                    int lane) {
+                                                    int lane, unsigned first) {
     using AT = ST;
     constexpr int UN = Unroll<AT>::U;
     __shared__ AT red[LT / 32][32][G];
@@ -642,8 +655,7 @@ __device__ __forceinline__ double adj_cells_chunked(const OpArgs<VT, ST> &a, ST 
     // take more; the result does not depend on the assignment because each
     // cell's sum of squares goes to the cell's slot
     unsigned *next_item = &a.sy->count[4];
-    unsigned nxt = 0;
-    if (lane == 0) nxt = atomicAdd(next_item, 1u);
+    unsigned nxt = first;   // lane 0: the item k_adj drew before its wait
     int64_t it = __shfl_sync(FULL, nxt, 0);
     for (; it < a.n_adj; it = __shfl_sync(FULL, nxt, 0)) {
         if (lane == 0) nxt = atomicAdd(next_item, 1u);
@@ -941,6 +953,16 @@ __global__ void __launch_bounds__(LT) k_step_sweep(const LsqrScalars *base, cons
 // generic kernel then no longer spilled).
 template <class VT, class ST, int FMT, int MB = (sizeof(VT) == 2 ? 3 : 4), int PATH = 0>
 __global__ void __launch_bounds__(LT, MB) k_fwd(OpArgs<VT, ST> a) {
+    if constexpr (FMT == FMT_BLK) {
+        // the first row's values do not depend on the adjoint: into L2 before the wait
+        const int64_t gw0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t r0 = gw0 * FWD_RB + ((threadIdx.x >> 4) & 1);
+        if ((threadIdx.x & 15) == 0 && r0 < a.m) {
+            const int64_t e0 = __ldg(a.row_cptr + r0), e1 = __ldg(a.row_cptr + r0 + 1);
+            prefetch_l2_bulk(a.val + e0 * (int64_t)a.nz, (uint64_t)(e1 - e0) * a.nz * sizeof(VT));
+        }
+    }
+    pdl_wait();
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
     using AT = ST;
@@ -1044,6 +1066,25 @@ static __device__ void sweep_step(LsqrScalars *base, LsqrScalars *ls, int L, dou
 // values three blocks per SM (up to 85 registers) measured faster than four.
 template <class VT, class ST, int FMT, int G>
 __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, ST> a, int init) {
+    // the blocked sweep's first work item is drawn, and its first values sent
+    // to L2, before the wait: the item counter was reset by the previous
+    // adjoint, which completed before the kernel this one waits for started
+    unsigned first = 0;
+    if constexpr (FMT == FMT_BLK) {
+        if ((threadIdx.x & 31) == 0) {
+            first = atomicAdd(&a.sy->count[4], 1u);
+            if (first < a.n_adj) {
+                const int h0 = __ldg(a.adj_item + 2 * first), q0 = __ldg(a.adj_item + 2 * first + 1);
+                const int cnt = __ldg(a.cell_cnt + h0);
+                const int q1 = min(q0 + a.adj_chunk, cnt);
+                if (q1 > q0)
+                    prefetch_l2_bulk(a.valB + (__ldg(a.cell_rptr + h0) + q0) * (int64_t)a.nz,
+                                     min((uint64_t)(q1 - q0) * a.nz * sizeof(VT), (uint64_t)4096));
+            }
+        }
+    }
+    pdl_wait();
+    pdl_allow_next();
     LsqrScalars *sc = a.sc;
     if (sc->done | sc->istop) return;
     if (FMT == FMT_BLK && G != G_ANY && adj_group(a.nz) != G) {   // another depth count
@@ -1064,13 +1105,14 @@ __global__ void __launch_bounds__(LT, sizeof(VT) == 2 ? 3 : 4) k_adj(OpArgs<VT, 
         if constexpr (FMT == FMT_BLK) {
             if constexpr (G == G_ANY) {
                 switch (adj_group(a.nz)) {
-                case 4: ss = adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
-                case 6: ss = adj_cells_chunked<VT, ST, 6>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
-                case 2: ss = adj_cells_chunked<VT, ST, 2>(a, ib, cv, wsm, lamr, init, gw, nw, lane); break;
-                default: ss = adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+                case 4: ss = adj_cells_chunked<VT, ST, 4>(a, ib, cv, wsm, lamr, init, gw, nw, lane, first); break;
+                case 6: ss = adj_cells_chunked<VT, ST, 6>(a, ib, cv, wsm, lamr, init, gw, nw, lane, first); break;
+                case 2: ss = adj_cells_chunked<VT, ST, 2>(a, ib, cv, wsm, lamr, init, gw, nw, lane, first); break;
+                default: ss = adj_cells_chunked<VT, ST, 1>(a, ib, cv, wsm, lamr, init, gw, nw, lane, first);
                 }
             } else {
-                ss = adj_cells_chunked<VT, ST, (G > 0 ? G : 1)>(a, ib, cv, wsm, lamr, init, gw, nw, lane);
+                ss = adj_cells_chunked<VT, ST, (G > 0 ? G : 1)>(a, ib, cv, wsm, lamr, init, gw, nw,
+                                                                lane, first);
             }
         } else {
             for (int64_t j = gw; j < a.n; j += nw) {
@@ -1260,6 +1302,7 @@ __global__ void k_pub_base(LsqrScalars *base) {
 // (one block, once both branches of the iteration have joined: the forward
 // wrote beta_{i+2} beside them).
 __global__ void __launch_bounds__(LT) k_pub(LsqrScalars *sc, const LsqrScalars *stage) {
+    pdl_allow_next();
     if (sc->step_pending) publish_step(sc, stage);
 }
 
@@ -1606,16 +1649,39 @@ template <class VT, class ST, int FMT> struct Solver {
     // ev (profile mode 2): four events recorded around the forward, the
     // update and the adjoint on the main stream, captured as event-record
     // nodes (external records: a plain record inside a capture only orders).
+    // A sweep launched with programmatic stream serialisation (see pdl_wait):
+    // the forward directly after the previous adjoint, the adjoint directly
+    // after k_pub.  Profile mode 2 puts event nodes between them and launches
+    // plainly.
+    template <class K, class... Args>
+    static void launch_dep(K kernel, unsigned grid, cudaStream_t s, bool pdl, Args... args) {
+        if (!pdl) {
+            kernel<<<grid, LT, 0, s>>>(args...);
+            return;
+        }
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(LT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, kernel, args...);
+    }
     static void launch_iter(pdst_handle *h, LsqrWork *w, const OpArgs<VT, ST> &a, cudaStream_t s,
                             const cudaEvent_t *ev = nullptr) {
+        const bool pdl = ev == nullptr;
         fork_step_update(h, w, a, s);
         if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
-        fwd_kernel<VT, ST, FMT>(h->nz)<<<w->grid_rows, LT, 0, s>>>(a);
+        launch_dep(fwd_kernel<VT, ST, FMT>(h->nz), w->grid_rows, s, pdl, a);
         if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
         cudaStreamWaitEvent(s, w->ev_join, 0);
         k_pub<<<1, LT, 0, s>>>(a.sc, a.sc_stage);
         if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-        adj_kernel<VT, ST, FMT>(h->nz)<<<w->grid_cols, LT, 0, s>>>(a, 0);
+        launch_dep(adj_kernel<VT, ST, FMT>(h->nz), w->grid_cols, s, pdl, a, 0);
         if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
     }
 
