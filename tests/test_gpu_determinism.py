@@ -55,3 +55,23 @@ def test_batched_repeat_identical(mid):
     o1, _, _ = pdst.lsqr_batched([h], [D], [p.w], lams, 40, 0.0, dtype="f32", tile_rows=8)
     o2, _, _ = pdst.lsqr_batched([h], [D], [p.w], lams, 40, 0.0, dtype="f32", tile_rows=8)
     assert np.array_equal(o1[0].cpu().numpy(), o2[0].cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_launch_modes_give_the_same_bits(mid, dtype):
+    """The graph replay launches each sweep with programmatic dependent launch
+    (its blocks scheduled while the kernel before it finishes); the profiled
+    replay launches the same kernels plainly between event nodes, and profile
+    mode 1 one at a time with the scalar step in line.  Same arithmetic in the
+    same order, so the iterates and estimates are identical bit for bit, with
+    the depth blocks as well."""
+    p, h, d = mid
+    h.set_block_precond(None, p.w, p.lam)
+    for precond in (0, 2):
+        kw = dict(dtype=dtype, fmt="blocked", conlim=1e300, precond=precond)
+        base = h.lsqr(d, p.w, p.lam, 40, 0.0, **kw)
+        for extra in ({"profile": 2}, {"profile": 1}, {"use_graph": False}):
+            r = h.lsqr(d, p.w, p.lam, 40, 0.0, **kw, **extra)
+            assert r.info["iters"] == base.info["iters"] == 40
+            assert r.info["rnorm"] == base.info["rnorm"], (precond, extra)
+            assert np.array_equal(r.m.cpu().numpy(), base.m.cpu().numpy()), (precond, extra)
